@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark: clipped Voronoi cells per second on one B300 (or N replicas).
+
+One step = one ``vd_compute`` through the C ABI: grid build, nearest-neighbour
+distances, seeding, the persistent clip-and-flood kernel and the per-site
+reduction (measure, centroid, neighbour CSR) for the whole workload.
+
+value   device-resident inputs; per-step CUDA events on the compute stream;
+        L2 flushed (256 MiB write) before every step, outside the events.
+e2e     the same metric through the public API with host buffers: pinned host
+        sites -> device, compute, results (measure, centroid, CSR) -> host.
+roofline  the clip kernel (dominant), FP32-ALU bound: algorithmic FLOPs (8 per
+        site-distance evaluation, counted by the library's counters) over its
+        event-timed duration, against SMs x 128 lanes x 2 x max SM clock.
+cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): independent replicas (different seeds), no data-path
+collective; value = cells of all ranks / max over ranks of the step time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "cube"
+METRIC = "clipped Voronoi cells/sec (3D, 1M sites) learned+batched vs plain GPU, oracle-exact"
+UNIT = "cells/s"
+DESC = {
+    "cube": "3D clipped VD: unit cube as 6 tets, 100,000 uniform sites (FP32, FP64-filtered signs)",
+    "shell": "3D clipped VD: tetrahedralised spherical shell (172,032 tets), 1,000,000 sites "
+             "(16-component Gaussian mixture sigma 0.02 + 10% uniform), FP32",
+    "cube2m": "3D clipped VD: unit cube as 6 tets, 2,000,000 uniform sites, FP32",
+    "square": "2D clipped VD: unit square as 2 triangles, 1,000 uniform sites, FP64",
+    "torus": "restricted VD: torus (500,000 triangles), 200,000 sites, FP32",
+}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s=15.0, seed=0):
+    """Oracle (FP64, all host threads) on a bounded sample of sites: cells/s."""
+    import numpy as np
+
+    import oracle as O
+
+    cores = os.cpu_count() or 1
+    o = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], nthreads=cores)
+    rng = np.random.default_rng(seed)
+    n = len(w["sites"])
+    pilot = rng.choice(n, min(n, 4 * cores), replace=False)
+    t0 = time.perf_counter()
+    o.site_pieces(pilot)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(n, max(len(pilot), len(pilot) * budget_s / dt)))
+    pick = rng.choice(n, k, replace=False)
+    t0 = time.perf_counter()
+    o.site_pieces(pick)
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all pieces of {k} random sites of the workload ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_2509_07175_b300 import inputs as I
+
+    w = I.workload(args.workload)
+    base = cpu_baseline(w, budget_s=min(10.0, max(2.0, 60.0 / max(1, args.steps + args.warmup))))
+    line = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * len(w["sites"]) / base["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": DESC.get(args.workload), "n_sites": len(w["sites"]),
+                       "n_simplices": len(w["simp"])},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(DESC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+
+    from paper_2509_07175_b300 import binding as B
+    from paper_2509_07175_b300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = I.workload(args.workload, seed=None if rank == 0 else I.SEED_BASE + 1000 + rank)
+    n = len(w["sites"])
+    d = B.diagram_from_workload(w)
+    # counters for the roofline numerator (an untimed run with the counters on)
+    d.set_options(stats=1)
+    rs = d.compute()
+    counts = rs["stats"]
+    d.set_options(timing=1)
+    for _ in range(args.warmup):
+        code, _r = d.compute_raw()
+        assert code == 0, B.ERRORS.get(code, code)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clip_ms = []
+    launches = 0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        code, r = d.compute_raw()
+        ends[k].record(stream)
+        assert code == 0, B.ERRORS.get(code, code)
+        clip_ms.append(r.phase_ms[3])
+        launches += int(r.stats[13])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        lt = torch.tensor([launches], device="cuda", dtype=torch.int64)
+        dist.all_reduce(lt)
+        launches = int(lt.item())
+    value = n * args.steps * world / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    dim = 2 if w["mode"] == B.MODE_2D else 3
+    dt = torch.float64 if w["f64"] else torch.float32
+    host_sites = torch.tensor(w["sites"][:, :dim], dtype=dt).pin_memory()
+    meas_h = torch.empty(n, dtype=dt).pin_memory()
+    cen_h = torch.empty((n, 3), dtype=dt).pin_memory()
+    off_h = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    nnz = int(rs["nbr_off"][-1].item())
+    idx_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+    d.set_options()
+    for _ in range(2):
+        d.update_sites_host(host_sites)
+        d.compute_raw()
+        d.copy_result_host(meas_h, cen_h, off_h, idx_h)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        d.update_sites_host(host_sites)
+        code, _r = d.compute_raw()
+        d.copy_result_host(meas_h, cen_h, off_h, idx_h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = n * args.steps * world / e2e_s
+    esz = 8 if w["f64"] else 4
+    h2d = n * dim * esz
+    d2h = n * esz + 3 * n * esz + (n + 1) * 8 + nnz * 4
+
+    if rank != 0:
+        d.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = _peaks()
+    sm = 148
+    try:
+        sm = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        pass
+    max_mhz = ck.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    peak_tflops = sm * 128 * 2 * max_mhz * 1e6 / 1e12
+    flops = 8.0 * counts["sites_scanned"]
+    clip_s = statistics.median(clip_ms) / 1e3 if clip_ms else float("nan")
+    achieved = flops / clip_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w["f64"] else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": DESC[args.workload], "n_sites": n,
+                   "n_simplices": len(w["simp"]), "pairs": counts["pairs"], "nonempty_pieces": counts["nonempty"],
+                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_flood (Alg. 3 clip + flood)", "bound": "alu", "achieved": achieved,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "peak_source": f"{sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                     "flops_per_launch": flops, "clip_ms": clip_s * 1e3,
+                     "clip_share": (clip_s * 1e3) / (total_ms / args.steps), "traffic": None},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "stats": {k: counts[k] for k in ("nn_queries", "corner_tests", "clips", "lambda_steps", "search_steps",
+                                         "fp64", "uncertain", "ties", "sites_scanned", "fallback")},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    d.close()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * vd.h -- C ABI of libvd: clipped (2D, 3D) and restricted (surface) Voronoi
+ * diagrams computed on the GPU by edge-based clipping driven by point-in-cell
+ * tests (Xiao, Cao, Chen, "Efficient Computation of Voronoi Diagrams Using
+ * Point-in-Cell Tests").
+ *
+ * Problem (Sec. 2.1, Eq. 1): sites v_1..v_n and a domain M made of simplices
+ * T_1..T_m (triangles in 2D or on a surface, tetrahedra in 3D).  The cell of v_i
+ * is Omega_i = { x : |x - v_i| <= |x - v_j| for all j }; the output is, for
+ * every site, Omega_i intersected with M: its measure (area or volume), its
+ * centroid and the sites whose cells share a face of positive measure with it
+ * (the positive face flags of Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *   - All device pointers are CUDA device addresses on the context's device.
+ *     Inputs are caller-owned and copied before the call returns or, for the
+ *     asynchronous calls, before any later call on the same stream runs.
+ *   - Results (vd_result, vd_pieces) point into memory owned by the context.
+ *     They stay valid until the next vd_compute / vd_update_sites /
+ *     vd_set_domain / vd_destroy on the same context.
+ *   - Errors are returned as negative codes (vd_strerror names them); no entry
+ *     point throws, aborts or prints.  A failed call leaves the context usable
+ *     unless the code is VD_ERR_CUDA.
+ *   - Work is enqueued on the context's stream (vd_set_stream; default: the
+ *     legacy default stream).
+ */
+#ifndef VD_H_
+#define VD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vd_ctx vd_ctx;
+
+enum {
+  VD_OK = 0,
+  VD_ERR_ARG = -1,        /* bad argument (null pointer, size, mode, dtype) */
+  VD_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  VD_ERR_OOM = -3,        /* device allocation failed */
+  VD_ERR_CAPACITY = -4,   /* a fixed capacity was exceeded (polytope corners or
+                             planes, work queue, pair set); results are invalid */
+  VD_ERR_LIMIT = -5,      /* a bounded loop or wait hit its limit; results invalid */
+  VD_ERR_DOMAIN = -6,     /* the mesh failed validation (bad index, zero-measure
+                             simplex, face shared by more than two simplices) */
+  VD_ERR_UNCERTAIN = -7,  /* reserved: a sign could not be certified even in FP64
+                             (reported through the stats, results still written) */
+  VD_ERR_STATE = -8       /* call out of order (e.g. vd_compute before vd_set_domain) */
+};
+
+enum { VD_F32 = 0, VD_F64 = 1 };
+
+/* dim / simplex_verts select the mode: (2,3) planar triangles, (3,3) surface
+ * triangles in R^3 (restricted diagram), (3,4) tetrahedra (clipped diagram) */
+enum { VD_MODE_2D = 2, VD_MODE_SURFACE = 3, VD_MODE_3D = 4 };
+
+/* statistics slots of vd_result.stats (counted only when vd_options.stats = 1,
+ * except the ones marked "always") */
+enum {
+  VD_STAT_PAIRS = 0,          /* (simplex, site) pairs processed (always) */
+  VD_STAT_NONEMPTY = 1,       /* pairs with a non-empty piece (always) */
+  VD_STAT_NN_QUERIES = 2,     /* nearest-site scans (point-in-cell and search) */
+  VD_STAT_CORNER_TESTS = 3,   /* point-in-cell tests on corners */
+  VD_STAT_CLIPS = 4,          /* clips performed */
+  VD_STAT_LAMBDA_STEPS = 5,   /* start-point steps of the improved search */
+  VD_STAT_SEARCH_STEPS = 6,   /* bisector-search steps */
+  VD_STAT_FP64 = 7,           /* sign decisions settled in FP64 (always) */
+  VD_STAT_UNCERTAIN = 8,      /* decisions not certified in FP64 (always) */
+  VD_STAT_TIES = 9,           /* exact ties (value zero), counted as inside (always) */
+  VD_STAT_SITES_SCANNED = 10, /* site-distance evaluations in nearest-site scans */
+  VD_STAT_LEARNED_HITS = 11,  /* bisectors found by the learned candidate shortcut */
+  VD_STAT_FALLBACK = 12,      /* searches that fell back to the certified witness */
+  VD_STAT_LAUNCHES = 13,      /* kernels launched by the call (always) */
+  VD_STAT_ILLCOND = 14,       /* corners too ill-conditioned for the FP32 filter (always) */
+  VD_STAT_ERROR_LINE = 15,    /* source line of the first device-side error (diagnostics) */
+  VD_STAT_DIAG = 16,          /* 16..23: first FP64 decision that was not certified or was an
+                                 exact tie: simplex, site, the 4 plane sources, tie flag, kind */
+  VD_STAT_N = 32
+};
+
+/* phases timed with CUDA events on the context stream when vd_options.timing = 1 */
+enum { VD_PHASE_GRID = 0, VD_PHASE_DELTA = 1, VD_PHASE_SEED = 2, VD_PHASE_CLIP = 3, VD_PHASE_REDUCE = 4,
+       VD_PHASE_N = 8 };
+
+typedef struct {
+  int learned;             /* 1: use the candidate lists set by vd_set_candidates */
+  int mapping;             /* 0: automatic (autotuned), 1: warp per pair, 2: half-warp per pair */
+  int chunk;               /* pairs claimed per queue access (0: automatic) */
+  int stats;               /* 1: collect the counters marked above */
+  int64_t queue_capacity;  /* pairs (0: automatic, 8 (n + m) + 4096) */
+  int max_clips;           /* clips per pair before VD_ERR_LIMIT (0: 256) */
+  int max_search;          /* bisector-search steps per clip (0: 256) */
+  int max_lambda;          /* start-point steps per clip (0: 64) */
+  double wait_limit_s;     /* longest wait of an idle worker on the queue (0: 10 s) */
+  int timing;              /* 1: time the phases of vd_compute with CUDA events */
+} vd_options;
+
+typedef struct {
+  int64_t n;               /* sites */
+  int64_t nnz;             /* total neighbour entries */
+  int64_t n_pieces;        /* non-empty pieces */
+  int dtype;               /* VD_F32 / VD_F64: element type of measure and centroid */
+  const void* measure;     /* device [n]: area or volume of Omega_i within M */
+  const void* centroid;    /* device [n*3]: centroid (v_i for an empty cell) */
+  const int64_t* nbr_off;  /* device [n+1]: CSR offsets */
+  const int32_t* nbr_idx;  /* device [nnz]: neighbours of each site, ascending */
+  int64_t stats[VD_STAT_N];
+  int status;              /* VD_OK or the first device-side error code */
+  double phase_ms[VD_PHASE_N]; /* per-phase device time (vd_options.timing = 1), else 0 */
+} vd_result;
+
+typedef struct {
+  int64_t n_pieces;        /* number of (simplex, site) pairs processed */
+  const int32_t* simplex;  /* device [n_pieces] */
+  const int32_t* site;     /* device [n_pieces] */
+  const void* measure;     /* device [n_pieces] (dtype of the context); 0 for empty pieces */
+  const void* moment;      /* device [n_pieces*3]: first moment in the frame of the site */
+  const int64_t* flag_off; /* device [n_pieces+1] */
+  const int32_t* flags;    /* device: face flags of positive measure; j >= 0: bisector with
+                              site j; -(b+1): face shared with simplex b; INT32_MIN: mesh
+                              boundary (Sec. 2.2) */
+} vd_pieces;
+
+/* Create a context for n sites of the given dimension (2 or 3) and dtype.
+ * sites: device pointer, n*dim elements of dtype, row-major; copied.
+ * Sec. 2.1 (the sites V).  Returns VD_ERR_ARG for n < 1, dim not in {2,3},
+ * dtype not in {VD_F32, VD_F64}. */
+int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype);
+
+/* Set the domain M = {T_a} (Sec. 2.1).  verts: device pointer, nv*dim elements of
+ * the context dtype; simplices: device pointer, m*simplex_verts int32 vertex
+ * indices (3: triangles, 4: tetrahedra).  Copied and validated (indices in
+ * range, non-zero measure, faces shared by at most two simplices); builds the
+ * simplex adjacency that initialises the negative face flags (Sec. 2.2) and the
+ * simplex locator used to seed pairs.  Synchronises the context stream. */
+int vd_set_domain(vd_ctx* ctx, const void* verts, int64_t nv, const int32_t* simplices, int64_t m,
+                  int simplex_verts);
+
+/* Replace the options (NULL restores the defaults). */
+int vd_set_options(vd_ctx* ctx, const vd_options* opt);
+
+/* Enqueue all later work on this cudaStream_t (NULL: legacy default stream). */
+int vd_set_stream(vd_ctx* ctx, void* cuda_stream);
+
+/* Replace the site coordinates (same n and dim; device pointer, copied). */
+int vd_update_sites(vd_ctx* ctx, const void* sites);
+
+/* Host-pointer variant of vd_update_sites (pinned or pageable host memory). */
+int vd_update_sites_host(vd_ctx* ctx, const void* sites_host);
+
+/* Compute the clipped / restricted diagram of the current sites (Alg. 3 for
+ * every (simplex, site) pair, pairs discovered by the flag propagation of
+ * Alg. 4 / Alg. 5, improved search of Sec. 5.1, grid search of Sec. 5.2).
+ * Synchronises the stream once at the end to read the status and counts.
+ * out may be NULL.  Returns the first device-side error, if any. */
+int vd_compute(vd_ctx* ctx, vd_result* out);
+
+/* Copy the per-site measure [n], centroid [n*3] (context dtype) and, when
+ * nbr_off is not NULL, the CSR (nbr_off [n+1] int64, nbr_idx [nnz] int32) of the
+ * last vd_compute to host memory.  nbr_idx must hold the nnz of that result. */
+int vd_copy_result_host(vd_ctx* ctx, void* measure, void* centroid, int64_t* nbr_off, int32_t* nbr_idx);
+
+/* Lloyd's method (Sec. 6.4, density 1): iters times { compute the diagram;
+ * v_i <- centroid_i (sites with empty cells stay) }.  use_graph = 1 captures one
+ * iteration in a CUDA graph and replays it; the host reads the status once at
+ * the end.  The last iteration's diagram is not recomputed for the final sites. */
+int vd_lloyd(vd_ctx* ctx, int iters, int use_graph);
+
+/* Copy the current site coordinates (n*3, context dtype) to a device buffer. */
+int vd_get_sites(vd_ctx* ctx, void* sites_out);
+
+/* Per-piece output of the last vd_compute (the clip topology). */
+int vd_get_pieces(vd_ctx* ctx, vd_pieces* out);
+
+/* Learned proposal (ranking of likely bisector neighbours): candidate site
+ * indices per site, device int32 [n*k], -1 = unused slot; copied.  They only
+ * order the search; every clip is still decided by the exact test, so the
+ * output does not change.  k = 0 clears them. */
+int vd_set_candidates(vd_ctx* ctx, const int32_t* cand, int k);
+
+/* Release everything owned by the context (NULL is allowed). */
+void vd_destroy(vd_ctx* ctx);
+
+/* Static string naming an error code. */
+const char* vd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VD_H_ */

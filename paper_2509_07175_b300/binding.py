@@ -1,0 +1,247 @@
+"""ctypes binding of libvd (include/vd.h): argument marshalling only.
+
+Every step of the computation runs in libvd's CUDA kernels; torch supplies the
+device memory (``tensor.data_ptr()``) and the stream.  Loading fails loudly if
+the library is missing or no CUDA device is present -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvd.so")
+
+VD_F32, VD_F64 = 0, 1
+MODE_2D, MODE_SURFACE, MODE_3D = 2, 3, 4
+FLAG_BOUNDARY = -(2 ** 31)
+STAT_NAMES = ("pairs", "nonempty", "nn_queries", "corner_tests", "clips", "lambda_steps", "search_steps",
+              "fp64", "uncertain", "ties", "sites_scanned", "learned_hits", "fallback", "launches", "illcond")
+PHASE_NAMES = ("grid", "delta", "seed", "clip", "reduce")
+
+ERRORS = {0: "ok", -1: "VD_ERR_ARG", -2: "VD_ERR_CUDA", -3: "VD_ERR_OOM", -4: "VD_ERR_CAPACITY",
+          -5: "VD_ERR_LIMIT", -6: "VD_ERR_DOMAIN", -7: "VD_ERR_UNCERTAIN", -8: "VD_ERR_STATE"}
+
+
+class VDError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({code})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("learned", ctypes.c_int), ("mapping", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("stats", ctypes.c_int), ("queue_capacity", ctypes.c_int64), ("max_clips", ctypes.c_int),
+                ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
+                ("timing", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_pieces", ctypes.c_int64),
+                ("dtype", ctypes.c_int), ("measure", ctypes.c_void_p), ("centroid", ctypes.c_void_p),
+                ("nbr_off", ctypes.c_void_p), ("nbr_idx", ctypes.c_void_p), ("stats", ctypes.c_int64 * 32),
+                ("status", ctypes.c_int), ("phase_ms", ctypes.c_double * 8)]
+
+
+class PiecesC(ctypes.Structure):
+    _fields_ = [("n_pieces", ctypes.c_int64), ("simplex", ctypes.c_void_p), ("site", ctypes.c_void_p),
+                ("measure", ctypes.c_void_p), ("moment", ctypes.c_void_p), ("flag_off", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libvd.so (raises if absent: the product path has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libvd.so not built ({path}); run paper_2509_07175_b300/build.py")
+    lib = ctypes.CDLL(path)
+    P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "vd_create": ([ctypes.POINTER(P), P, I64, I, I], I),
+        "vd_set_domain": ([P, P, I64, P, I64, I], I),
+        "vd_set_options": ([P, ctypes.POINTER(Options)], I),
+        "vd_set_stream": ([P, P], I),
+        "vd_update_sites": ([P, P], I),
+        "vd_update_sites_host": ([P, P], I),
+        "vd_compute": ([P, ctypes.POINTER(Result)], I),
+        "vd_copy_result_host": ([P, P, P, P, P], I),
+        "vd_lloyd": ([P, I, I], I),
+        "vd_get_sites": ([P, P], I),
+        "vd_get_pieces": ([P, ctypes.POINTER(PiecesC)], I),
+        "vd_set_candidates": ([P, P, I], I),
+        "vd_destroy": ([P], None),
+        "vd_strerror": ([I], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return ["vd_create", "vd_set_domain", "vd_set_options", "vd_set_stream", "vd_update_sites",
+            "vd_update_sites_host", "vd_compute", "vd_copy_result_host", "vd_lloyd", "vd_get_sites",
+            "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror"]
+
+
+class _DevArray:
+    """Borrowed device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+def _view(ptr, shape, dtype):
+    typestr = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4", torch.int64: "<i8"}[dtype]
+    n = 1
+    for s in shape:
+        n *= s
+    if n == 0 or not ptr:
+        return torch.zeros(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
+def _check(code, where):
+    if code != 0:
+        raise VDError(code, where)
+
+
+class Diagram:
+    """One site set and one simplicial domain on the current CUDA device.
+
+    sites: (n, dim) float32 or float64 CUDA tensor (dim 2 or 3).
+    verts: (nv, dim) CUDA tensor of the same dtype; simplices: (m, 3|4) int32.
+    """
+
+    def __init__(self, sites, verts, simplices, options: dict | None = None, stream=None):
+        lib = load()
+        if not (sites.is_cuda and verts.is_cuda and simplices.is_cuda):
+            raise ValueError("inputs must be CUDA tensors")
+        self.dtype = sites.dtype
+        self.n, self.dim = sites.shape
+        self._keep = []
+        h = ctypes.c_void_p()
+        s = sites.contiguous()
+        _check(lib.vd_create(ctypes.byref(h), s.data_ptr(), self.n, self.dim,
+                             VD_F64 if self.dtype == torch.float64 else VD_F32), "vd_create")
+        self._h = h
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        _check(lib.vd_set_stream(h, ctypes.c_void_p(st.cuda_stream)), "vd_set_stream")
+        if options:
+            self.set_options(**options)
+        v = verts.to(self.dtype).contiguous()
+        t = simplices.to(torch.int32).contiguous()
+        self.m, self.k = t.shape
+        _check(lib.vd_set_domain(h, v.data_ptr(), v.shape[0], t.data_ptr(), self.m, self.k), "vd_set_domain")
+        self.result = None
+
+    def set_options(self, **kw):
+        o = Options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        _check(load().vd_set_options(self._h, ctypes.byref(o)), "vd_set_options")
+
+    def update_sites(self, sites):
+        s = sites.to(self.dtype).contiguous()
+        _check(load().vd_update_sites(self._h, s.data_ptr()), "vd_update_sites")
+
+    def update_sites_host(self, sites_host):
+        _check(load().vd_update_sites_host(self._h, sites_host.data_ptr()), "vd_update_sites_host")
+
+    def compute(self, check=True):
+        """Run the diagram; returns dict of torch tensors (copies) and stats."""
+        r = Result()
+        code = load().vd_compute(self._h, ctypes.byref(r))
+        if check:
+            _check(code, "vd_compute")
+        self.result = r
+        return self._pack(r, code)
+
+    def compute_raw(self):
+        """vd_compute with no copies (for timing); returns the status code."""
+        r = Result()
+        return load().vd_compute(self._h, ctypes.byref(r)), r
+
+    def _pack(self, r, code):
+        n = int(r.n)
+        out = {
+            "status": code,
+            "measure": _view(r.measure, (n,), self.dtype).clone(),
+            "centroid": _view(r.centroid, (n, 3), self.dtype).clone(),
+            "nbr_off": _view(r.nbr_off, (n + 1,), torch.int64).clone(),
+            "nbr_idx": _view(r.nbr_idx, (int(r.nnz),), torch.int32).clone(),
+            "n_pieces": int(r.n_pieces),
+            "stats": dict(zip(STAT_NAMES, [int(x) for x in r.stats][:len(STAT_NAMES)]),
+                          error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]]),
+            "phase_ms": dict(zip(PHASE_NAMES, [float(x) for x in r.phase_ms][:len(PHASE_NAMES)])),
+        }
+        return out
+
+    def copy_result_host(self, measure, centroid, nbr_off=None, nbr_idx=None):
+        f = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+        _check(load().vd_copy_result_host(self._h, f(measure), f(centroid), f(nbr_off), f(nbr_idx)),
+               "vd_copy_result_host")
+
+    def pieces(self):
+        p = PiecesC()
+        _check(load().vd_get_pieces(self._h, ctypes.byref(p)), "vd_get_pieces")
+        np_ = int(p.n_pieces)
+        off = _view(p.flag_off, (np_ + 1,), torch.int64).clone()
+        nf = int(off[-1].item()) if np_ else 0
+        return {
+            "simplex": _view(p.simplex, (np_,), torch.int32).clone(),
+            "site": _view(p.site, (np_,), torch.int32).clone(),
+            "measure": _view(p.measure, (np_,), self.dtype).clone(),
+            "moment": _view(p.moment, (np_, 3), self.dtype).clone(),
+            "flag_off": off,
+            "flags": _view(p.flags, (nf,), torch.int32).clone(),
+        }
+
+    def lloyd(self, iters, use_graph=True):
+        _check(load().vd_lloyd(self._h, int(iters), int(bool(use_graph))), "vd_lloyd")
+
+    def sites(self):
+        out = torch.empty((self.n, 3), dtype=self.dtype, device="cuda")
+        _check(load().vd_get_sites(self._h, out.data_ptr()), "vd_get_sites")
+        torch.cuda.synchronize()
+        return out
+
+    def set_candidates(self, cand):
+        if cand is None:
+            _check(load().vd_set_candidates(self._h, None, 0), "vd_set_candidates")
+            return
+        c = cand.to(torch.int32).contiguous()
+        self._keep.append(c)
+        _check(load().vd_set_candidates(self._h, c.data_ptr(), c.shape[1]), "vd_set_candidates")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def diagram_from_workload(w: dict, device="cuda", options=None):
+    """Build a Diagram from an ``inputs.workload`` dict."""
+    dt = torch.float64 if w["f64"] else torch.float32
+    dim = 2 if w["mode"] == MODE_2D else 3
+    s = torch.tensor(w["sites"][:, :dim], dtype=dt, device=device)
+    v = torch.tensor(w["verts"][:, :dim], dtype=dt, device=device)
+    t = torch.tensor(w["simp"], dtype=torch.int32, device=device)
+    return Diagram(s, v, t, options=options)

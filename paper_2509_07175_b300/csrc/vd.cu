@@ -1,0 +1,783 @@
+// vd.cu -- libvd host side: the C ABI declared in include/vd.h.
+//
+// One context holds one site set and one domain on one device.  vd_compute
+// enqueues, on the context stream and without host synchronisation until its
+// final status read: grid build -> nearest-neighbour distances -> seeding ->
+// persistent clip-and-flood -> per-site reduction.  The same sequence (plus the
+// Lloyd update) is what vd_lloyd captures into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vd_kernels.cuh"
+
+using namespace vd;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct vd_ctx {
+  int dim = 3, dtype = VD_F32, mode = 0, k = 0;
+  long long n = 0, nv = 0, m = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  int device = 0, nsm = 0;
+  vd_options opt;
+  std::vector<void*> allocs;      // everything owned, freed by vd_destroy
+  std::vector<void*> dom_allocs;  // owned by the current domain
+  void* sites = nullptr;          // n*3 (T)
+  void* stage = nullptr;          // n*dim (T) upload staging
+  void* verts = nullptr;
+  int* simp = nullptr;
+  int* adj = nullptr;
+  signed char* fsgn = nullptr;
+  int* loc_start = nullptr;
+  int* loc_items = nullptr;
+  Locator L{};
+  int gx = 0, gy = 0, gz = 0;
+  double ox = 0, oy = 0, oz = 0, h = 1;
+  long long G = 0;
+  int *cellid = nullptr, *ccount = nullptr, *cstart = nullptr, *ccur = nullptr;
+  void* gs = nullptr;
+  void* delta = nullptr;
+  unsigned long long *hash = nullptr, *queue = nullptr, *ctr = nullptr;
+  unsigned long long hmask = 0;
+  long long qcap = 0, fcap = 0;
+  void *pmeas = nullptr, *pm1 = nullptr;
+  long long* pfoff = nullptr;
+  int *pfcnt = nullptr, *pflags = nullptr;
+  int *scnt = nullptr, *soff = nullptr, *scur = nullptr, *slist = nullptr, *fc = nullptr, *foff = nullptr,
+      *tmp = nullptr, *ucnt = nullptr, *nidx = nullptr;
+  long long* noff = nullptr;
+  void *measure = nullptr, *centroid = nullptr;
+  int* status = nullptr;
+  unsigned long long* stats = nullptr;
+  void* scan_tmp = nullptr;
+  int *xs = nullptr, *xi = nullptr, *xflags = nullptr;
+  long long* xoff = nullptr;
+  int* cand = nullptr;
+  int ncand = 0;
+  int flood_grid = 0;
+  size_t flood_smem = 0;
+  bool have_domain = false;
+  long long last_pairs = 0, last_nnz = 0, last_nonempty = 0;
+  int last_status = 0;
+  int last_where = 0;          // source line of the first device-side error
+  unsigned long long last_stats[VD_STAT_N] = {0};
+  bool computed = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaEvent_t ev[VD_PHASE_N + 1] = {};
+  bool timing_now = false;     // events recorded by the current enqueue
+  int launches = 0;            // kernels enqueued by the current enqueue
+  double last_phase_ms[VD_PHASE_N] = {0};
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      return e_ == cudaErrorMemoryAllocation ? VD_ERR_OOM : VD_ERR_CUDA; \
+    }                                           \
+  } while (0)
+
+static vd_options default_options() {
+  vd_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.mapping = 1;
+  return o;
+}
+
+static void resolve_options(vd_options& o) {
+  if (o.max_clips <= 0) o.max_clips = 256;
+  if (o.max_search <= 0) o.max_search = 256;
+  if (o.max_lambda <= 0) o.max_lambda = 64;
+  if (!(o.wait_limit_s > 0)) o.wait_limit_s = 10.0;
+}
+
+template <typename P>
+static int dalloc(vd_ctx* c, P*& p, size_t count, bool domain) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(P));
+  if (e != cudaSuccess) return VD_ERR_OOM;
+  (domain ? c->dom_allocs : c->allocs).push_back(q);
+  p = static_cast<P*>(q);
+  return VD_OK;
+}
+
+#define DALLOC(ptr, T_, count, dom)                          \
+  do {                                                       \
+    T_* tmp_ = nullptr;                                      \
+    int rc_ = dalloc(c, tmp_, (size_t)(count), dom);         \
+    if (rc_) return rc_;                                     \
+    ptr = tmp_;                                              \
+  } while (0)
+
+static size_t tsize(int dtype) { return dtype == VD_F64 ? 8 : 4; }
+
+static void free_domain(vd_ctx* c) {
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  for (void* p : c->dom_allocs) cudaFree(p);
+  c->dom_allocs.clear();
+  c->have_domain = false;
+  c->computed = false;
+}
+
+// ---------------------------------------------------------------------------
+// device context view
+// ---------------------------------------------------------------------------
+template <typename T>
+static Dev<T> make_dev(vd_ctx* c) {
+  Dev<T> D;
+  std::memset(&D, 0, sizeof(D));
+  D.mode = c->mode; D.n = (int)c->n; D.m = (int)c->m; D.k = c->k;
+  D.sites = (const T*)c->sites; D.verts = (const T*)c->verts; D.simp = c->simp; D.adj = c->adj; D.fsgn = c->fsgn;
+  D.delta = (const T*)c->delta;
+  D.G.gs = (const typename Prec<T>::V4*)c->gs; D.G.cstart = c->cstart;
+  D.G.gx = c->gx; D.G.gy = c->gy; D.G.gz = c->gz;
+  D.G.ox = (T)c->ox; D.G.oy = (T)c->oy; D.G.oz = (T)c->oz; D.G.h = (T)c->h; D.G.ih = (T)(1.0 / c->h);
+  D.cand = c->cand; D.ncand = c->ncand;
+  D.hash = c->hash; D.hmask = c->hmask; D.queue = c->queue; D.qcap = c->qcap; D.ctr = c->ctr;
+  D.pmeas = (T*)c->pmeas; D.pm1 = (T*)c->pm1; D.pfoff = c->pfoff; D.pfcnt = c->pfcnt; D.pflags = c->pflags;
+  D.fcap = c->fcap;
+  D.status = c->status; D.stats = c->stats; D.want_stats = c->opt.stats;
+  D.max_clips = c->opt.max_clips; D.max_search = c->opt.max_search; D.max_lambda = c->opt.max_lambda;
+  D.wait_ns = (long long)(c->opt.wait_limit_s * 1e9);
+  return D;
+}
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)std::max<long long>(1, (n + t - 1) / t); }
+
+template <typename In, typename Out>
+static void scan_excl(cudaStream_t s, const In* in, Out* out, long long n, Out* tmp) {
+  long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nb <= 1) {
+    k_scan_tile<In, Out><<<1, SCAN_T, 0, s>>>(in, out, nullptr, n);
+    return;
+  }
+  Out* bs = tmp;
+  Out* bo = tmp + nb;
+  k_scan_tile<In, Out><<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, bs, n);
+  scan_excl<Out, Out>(s, bs, bo, nb, tmp + 2 * nb);
+  k_scan_add<Out><<<nblk(n, 256), 256, 0, s>>>(out, bo, n);
+}
+
+static int scan_launches(long long n) {
+  long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  return nb <= 1 ? 1 : 2 + scan_launches(nb);
+}
+
+static size_t scan_tmp_elems(long long n) {
+  size_t t = 0;
+  long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  while (nb > 1) { t += 2 * nb; nb = (nb + SCAN_TILE - 1) / SCAN_TILE; }
+  return t + 16;
+}
+
+// everything of one diagram computation, enqueued on c->stream (graph-capturable)
+static inline void mark(vd_ctx* c, int k) {
+  if (c->timing_now) cudaEventRecord(c->ev[k], c->stream);
+}
+
+template <typename T, int MODE>
+static void enqueue_compute(vd_ctx* c) {
+  cudaStream_t s = c->stream;
+  Dev<T> D = make_dev<T>(c);
+  c->launches = 0;
+  mark(c, 0);
+  cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * VD_STAT_N, s);
+  cudaMemsetAsync(c->ctr, 0, sizeof(unsigned long long) * CTR_N, s);
+  cudaMemsetAsync(c->hash, 0xFF, sizeof(unsigned long long) * (c->hmask + 1), s);
+  cudaMemsetAsync(c->queue, 0xFF, sizeof(unsigned long long) * c->qcap, s);
+  cudaMemsetAsync(c->ccount, 0, sizeof(int) * (c->G + 1), s);
+  cudaMemsetAsync(c->ccur, 0, sizeof(int) * c->G, s);
+  unsigned bn = nblk(c->n, 256);
+  k_cell_count<T><<<bn, 256, 0, s>>>(D, c->cellid, c->ccount);
+  scan_excl<int, int>(s, c->ccount, c->cstart, c->G + 1, (int*)c->scan_tmp);
+  k_cell_scatter<T><<<bn, 256, 0, s>>>(D, c->cellid, c->cstart, c->ccur, (typename Prec<T>::V4*)c->gs);
+  c->launches += 2 + scan_launches(c->G + 1);
+  mark(c, 1);
+  k_delta<T><<<nblk(c->n, 128), 128, 0, s>>>(D, (T*)c->delta);
+  mark(c, 2);
+  k_seed_simplex<T><<<nblk(c->m, 128), 128, 0, s>>>(D);
+  if (MODE != VD_MODE_SURFACE) k_seed_site<T><<<nblk(c->n, 128), 128, 0, s>>>(D, c->L);
+  c->launches += MODE != VD_MODE_SURFACE ? 3 : 2;
+  mark(c, 3);
+  k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D);
+  c->launches += 1;
+  mark(c, 4);
+  cudaMemsetAsync(c->scnt, 0, sizeof(int) * (c->n + 1), s);
+  cudaMemsetAsync(c->scur, 0, sizeof(int) * c->n, s);
+  cudaMemsetAsync(c->fc, 0, sizeof(int) * (c->n + 1), s);
+  cudaMemsetAsync(c->ucnt, 0, sizeof(int) * (c->n + 1), s);
+  unsigned pg = (unsigned)std::max(1, c->nsm * 8);
+  k_site_count<T><<<pg, 256, 0, s>>>(D, c->scnt);
+  scan_excl<int, int>(s, c->scnt, c->soff, c->n + 1, (int*)c->scan_tmp);
+  k_site_fill<T><<<pg, 256, 0, s>>>(D, c->soff, c->scur, c->slist);
+  unsigned bs = nblk(c->n, 128);
+  k_site_reduce<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, (T*)c->measure, (T*)c->centroid, c->fc);
+  scan_excl<int, int>(s, c->fc, c->foff, c->n + 1, (int*)c->scan_tmp);
+  k_site_nbr<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, c->foff, c->tmp, c->ucnt);
+  scan_excl<int, long long>(s, c->ucnt, c->noff, c->n + 1, (long long*)c->scan_tmp);
+  k_site_nbr_copy<<<bs, 128, 0, s>>>((int)c->n, c->foff, c->tmp, c->noff, c->nidx);
+  c->launches += 5 + 3 * scan_launches(c->n + 1);
+  mark(c, 5);
+}
+
+static void enqueue_any(vd_ctx* c) {
+  if (c->dtype == VD_F64) {
+    enqueue_compute<double, VD_MODE_2D>(c);  // checked at vd_set_domain: FP64 runs the 2D path
+  } else if (c->mode == VD_MODE_3D) {
+    enqueue_compute<float, VD_MODE_3D>(c);
+  } else if (c->mode == VD_MODE_SURFACE) {
+    enqueue_compute<float, VD_MODE_SURFACE>(c);
+  } else {
+    enqueue_compute<float, VD_MODE_2D>(c);
+  }
+}
+
+static void enqueue_lloyd(vd_ctx* c) {
+  unsigned bn = nblk(c->n, 256);
+  if (c->dtype == VD_F64)
+    k_lloyd<double><<<bn, 256, 0, c->stream>>>((int)c->n, (double*)c->sites, (const double*)c->measure,
+                                              (const double*)c->centroid);
+  else
+    k_lloyd<float><<<bn, 256, 0, c->stream>>>((int)c->n, (float*)c->sites, (const float*)c->measure,
+                                             (const float*)c->centroid);
+}
+
+template <typename T, int MODE>
+static int flood_config(vd_ctx* c) {
+  using W = typename WarpOf<T, MODE>::type;
+  c->flood_smem = sizeof(W) * FLOOD_WARPS;
+  CK(cudaFuncSetAttribute(k_flood<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->flood_smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood<T, MODE>, FLOOD_WARPS * 32, c->flood_smem));
+  c->flood_grid = std::max(1, per_sm) * c->nsm;
+  return VD_OK;
+}
+
+static int read_status(vd_ctx* c) {
+  unsigned long long ctr[CTR_N];
+  int st = 0, where = 0;
+  long long nnz = 0;
+  int nonempty = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(ctr, c->ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&where, c->status + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  c->last_where = where;
+  CK(cudaMemcpy(c->last_stats, c->stats, sizeof(c->last_stats), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&nnz, c->noff + c->n, sizeof(long long), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&nonempty, c->soff + c->n, sizeof(int), cudaMemcpyDeviceToHost));
+  c->last_pairs = (long long)std::min<unsigned long long>(ctr[CTR_TAIL], (unsigned long long)c->qcap);
+  c->last_nnz = nnz;
+  c->last_nonempty = nonempty;
+  c->last_stats[VD_STAT_PAIRS] = (unsigned long long)c->last_pairs;
+  c->last_stats[VD_STAT_NONEMPTY] = (unsigned long long)nonempty;
+  if (st == 0 && ctr[CTR_TAIL] > (unsigned long long)c->qcap) st = VD_ERR_CAPACITY;
+  c->last_status = st;
+  c->computed = true;
+  c->last_stats[VD_STAT_LAUNCHES] = (unsigned long long)c->launches;
+  for (int k = 0; k < VD_PHASE_N; ++k) c->last_phase_ms[k] = 0;
+  if (c->timing_now) {
+    const int map[5] = {VD_PHASE_GRID, VD_PHASE_DELTA, VD_PHASE_SEED, VD_PHASE_CLIP, VD_PHASE_REDUCE};
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]) == cudaSuccess) c->last_phase_ms[map[k]] = ms;
+    }
+  }
+  return st;
+}
+
+static void fill_result(vd_ctx* c, vd_result* out) {
+  if (!out) return;
+  out->n = c->n;
+  out->nnz = c->last_nnz;
+  out->n_pieces = c->last_nonempty;
+  out->dtype = c->dtype;
+  out->measure = c->measure;
+  out->centroid = c->centroid;
+  out->nbr_off = (const int64_t*)c->noff;
+  out->nbr_idx = c->nidx;
+  std::memcpy(out->stats, c->last_stats, sizeof(out->stats));
+  out->status = c->last_status;
+  out->stats[VD_STAT_ERROR_LINE] = c->last_where;
+  for (int k = 0; k < VD_PHASE_N; ++k) out->phase_ms[k] = c->last_phase_ms[k];
+}
+
+// ---------------------------------------------------------------------------
+// host-side domain preparation (once per domain)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FaceKey {
+  int v[3];
+  long long s;
+  int f;
+  bool operator<(const FaceKey& o) const {
+    if (v[0] != o.v[0]) return v[0] < o.v[0];
+    if (v[1] != o.v[1]) return v[1] < o.v[1];
+    return v[2] < o.v[2];
+  }
+  bool same(const FaceKey& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2]; }
+};
+
+}  // namespace
+
+static int build_adjacency(int k, long long m, const std::vector<int>& simp, std::vector<int>& adj) {
+  std::vector<FaceKey> F((size_t)(m * k));
+  for (long long a = 0; a < m; ++a)
+    for (int f = 0; f < k; ++f) {
+      FaceKey& q = F[(size_t)(a * k + f)];
+      int c = 0;
+      for (int t = 0; t < k; ++t)
+        if (t != f) q.v[c++] = simp[(size_t)(a * k + t)];
+      if (c == 2) q.v[2] = -1;
+      std::sort(q.v, q.v + c);
+      q.s = a;
+      q.f = f;
+    }
+  std::sort(F.begin(), F.end());
+  adj.assign((size_t)(m * k), -1);
+  for (size_t t = 0; t < F.size();) {
+    size_t u = t + 1;
+    while (u < F.size() && F[t].same(F[u])) ++u;
+    if (u - t > 2) return VD_ERR_DOMAIN;
+    if (u - t == 2) {
+      adj[(size_t)(F[t].s * k + F[t].f)] = (int)F[t + 1].s;
+      adj[(size_t)(F[t + 1].s * k + F[t + 1].f)] = (int)F[t].s;
+    }
+    t = u;
+  }
+  return VD_OK;
+}
+
+extern "C" {
+
+const char* vd_strerror(int code) {
+  switch (code) {
+    case VD_OK: return "ok";
+    case VD_ERR_ARG: return "invalid argument";
+    case VD_ERR_CUDA: return "CUDA runtime error";
+    case VD_ERR_OOM: return "device allocation failed";
+    case VD_ERR_CAPACITY: return "capacity exceeded (polytope, queue, pair set or flag buffer)";
+    case VD_ERR_LIMIT: return "bounded loop or wait hit its limit";
+    case VD_ERR_DOMAIN: return "invalid domain mesh";
+    case VD_ERR_UNCERTAIN: return "sign not certified in FP64";
+    case VD_ERR_STATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype) {
+  if (!out || !sites || n < 1 || n > (int64_t)0x3fffffff || (dim != 2 && dim != 3) ||
+      (dtype != VD_F32 && dtype != VD_F64))
+    return VD_ERR_ARG;
+  vd_ctx* c = new (std::nothrow) vd_ctx();
+  if (!c) return VD_ERR_OOM;
+  c->n = n; c->dim = dim; c->dtype = dtype;
+  c->opt = default_options();
+  resolve_options(c->opt);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) { delete c; return VD_ERR_CUDA; }
+  size_t ts = tsize(dtype);
+  int rc = VD_OK;
+  {
+    char* p = nullptr;
+    rc = dalloc(c, p, (size_t)n * 3 * ts, false);
+    c->sites = p;
+    if (!rc) { rc = dalloc(c, p, (size_t)n * dim * ts, false); c->stage = p; }
+    if (!rc) { int* st = nullptr; rc = dalloc(c, st, 2, false); c->status = st; }
+    if (!rc) { unsigned long long* s = nullptr; rc = dalloc(c, s, VD_STAT_N, false); c->stats = s; }
+  }
+  if (rc) { vd_destroy(c); return rc; }
+  *out = c;
+  rc = vd_update_sites(c, sites);
+  if (rc) { vd_destroy(c); *out = nullptr; return rc; }
+  cudaStreamSynchronize(c->stream);
+  return VD_OK;
+}
+
+int vd_update_sites(vd_ctx* c, const void* sites) {
+  if (!c || !sites) return VD_ERR_ARG;
+  unsigned bn = nblk(c->n, 256);
+  if (c->dtype == VD_F64) k_widen<double, double><<<bn, 256, 0, c->stream>>>((const double*)sites, (double*)c->sites, c->n, c->dim);
+  else k_widen<float, float><<<bn, 256, 0, c->stream>>>((const float*)sites, (float*)c->sites, c->n, c->dim);
+  CK(cudaGetLastError());
+  return VD_OK;
+}
+
+int vd_update_sites_host(vd_ctx* c, const void* host) {
+  if (!c || !host) return VD_ERR_ARG;
+  size_t bytes = (size_t)c->n * c->dim * tsize(c->dtype);
+  CK(cudaMemcpyAsync(c->stage, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  return vd_update_sites(c, c->stage);
+}
+
+int vd_get_sites(vd_ctx* c, void* out) {
+  if (!c || !out) return VD_ERR_ARG;
+  CK(cudaMemcpyAsync(out, c->sites, (size_t)c->n * 3 * tsize(c->dtype), cudaMemcpyDeviceToDevice, c->stream));
+  return VD_OK;
+}
+
+int vd_set_stream(vd_ctx* c, void* s) {
+  if (!c) return VD_ERR_ARG;
+  c->stream = (cudaStream_t)s;
+  return VD_OK;
+}
+
+int vd_set_options(vd_ctx* c, const vd_options* o) {
+  if (!c) return VD_ERR_ARG;
+  c->opt = o ? *o : default_options();
+  resolve_options(c->opt);
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  return VD_OK;
+}
+
+int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simplices, int64_t m, int sv) {
+  if (!c || !verts || !simplices || nv < 3 || m < 1 || m > (int64_t)0x3fffffff) return VD_ERR_ARG;
+  int mode;
+  if (c->dim == 2 && sv == 3) mode = VD_MODE_2D;
+  else if (c->dim == 3 && sv == 3) mode = VD_MODE_SURFACE;
+  else if (c->dim == 3 && sv == 4) mode = VD_MODE_3D;
+  else return VD_ERR_ARG;
+  if (c->dtype == VD_F64 && mode != VD_MODE_2D) return VD_ERR_ARG;  // FP64 path: planar only
+  free_domain(c);
+  c->mode = mode; c->k = sv; c->nv = nv; c->m = m;
+  size_t ts = tsize(c->dtype);
+  // host copies for validation and set-up
+  std::vector<double> hv((size_t)nv * 3, 0.0);
+  {
+    std::vector<char> raw((size_t)nv * c->dim * ts);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(raw.data(), verts, raw.size(), cudaMemcpyDeviceToHost));
+    for (long long v = 0; v < nv; ++v)
+      for (int d = 0; d < c->dim; ++d)
+        hv[(size_t)(3 * v + d)] = c->dtype == VD_F64 ? ((double*)raw.data())[v * c->dim + d]
+                                                     : (double)((float*)raw.data())[v * c->dim + d];
+  }
+  std::vector<int> hs((size_t)(m * sv));
+  CK(cudaMemcpy(hs.data(), simplices, hs.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int x : hs)
+    if (x < 0 || x >= nv) return VD_ERR_DOMAIN;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (long long v = 0; v < nv; ++v)
+    for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], hv[3 * v + d]); hi[d] = std::max(hi[d], hv[3 * v + d]); }
+  double measure = 0;
+  std::vector<signed char> fs((size_t)(m * sv), 1);
+  for (long long a = 0; a < m; ++a) {
+    const double* P[4];
+    for (int l = 0; l < sv; ++l) P[l] = &hv[3 * (size_t)hs[(size_t)(a * sv + l)]];
+    if (sv == 4) {
+      double u[3], v[3], w[3];
+      for (int d = 0; d < 3; ++d) { u[d] = P[1][d] - P[0][d]; v[d] = P[2][d] - P[0][d]; w[d] = P[3][d] - P[0][d]; }
+      double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) + u[2] * (v[0] * w[1] - v[1] * w[0]);
+      if (!(std::fabs(det) > 0)) return VD_ERR_DOMAIN;
+      measure += std::fabs(det) / 6.0;
+      for (int f = 0; f < 4; ++f) {
+        int l0 = f == 0 ? 1 : 0, l1 = f <= 1 ? 2 : 1, l2 = f <= 2 ? 3 : 2;
+        double e1[3], e2[3], dd[3];
+        for (int d = 0; d < 3; ++d) { e1[d] = P[l1][d] - P[l0][d]; e2[d] = P[l2][d] - P[l0][d]; dd[d] = P[f][d] - P[l0][d]; }
+        double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2], nz = e1[0] * e2[1] - e1[1] * e2[0];
+        fs[(size_t)(4 * a + f)] = (nx * dd[0] + ny * dd[1] + nz * dd[2]) < 0 ? 1 : -1;
+      }
+    } else {
+      double u[3], v[3];
+      for (int d = 0; d < 3; ++d) { u[d] = P[1][d] - P[0][d]; v[d] = P[2][d] - P[0][d]; }
+      double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+      double ar = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+      if (!(ar > 0)) return VD_ERR_DOMAIN;
+      measure += ar;
+    }
+  }
+  std::vector<int> hadj;
+  int rc = build_adjacency(sv, m, hs, hadj);
+  if (rc) return rc;
+  // device copies of the mesh
+  {
+    char* p = nullptr;
+    rc = dalloc(c, p, (size_t)nv * 3 * ts, true); if (rc) return rc;
+    c->verts = p;
+    if (c->dtype == VD_F64) k_widen<double, double><<<nblk(nv, 256), 256, 0, c->stream>>>((const double*)verts, (double*)p, nv, c->dim);
+    else k_widen<float, float><<<nblk(nv, 256), 256, 0, c->stream>>>((const float*)verts, (float*)p, nv, c->dim);
+    CK(cudaGetLastError());
+  }
+  DALLOC(c->simp, int, m * sv, true);
+  DALLOC(c->adj, int, m * sv, true);
+  DALLOC(c->fsgn, signed char, m * sv, true);
+  CK(cudaMemcpy(c->simp, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->adj, hadj.data(), hadj.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->fsgn, fs.data(), fs.size(), cudaMemcpyHostToDevice));
+  // simplex locator: bins over the mesh box, each listing the simplices whose box meets it
+  if (mode != VD_MODE_SURFACE) {
+    int dims = mode == VD_MODE_2D ? 2 : 3;
+    double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    double vol = 1;
+    for (int d = 0; d < dims; ++d) vol *= std::max(ext[d], 1e-30);
+    double bs = std::pow(vol / std::max<double>(1, (double)m), 1.0 / dims);
+    int nb[3] = {1, 1, 1};
+    for (int d = 0; d < dims; ++d) nb[d] = std::max(1, std::min(1024, (int)std::ceil(ext[d] / bs)));
+    double bh = 0;
+    for (int d = 0; d < dims; ++d) bh = std::max(bh, ext[d] / nb[d]);
+    bh *= 1.000001;
+    std::vector<std::vector<int>> bins((size_t)nb[0] * nb[1] * nb[2]);
+    for (long long a = 0; a < m; ++a) {
+      double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
+      for (int l = 0; l < sv; ++l)
+        for (int d = 0; d < 3; ++d) {
+          double x = hv[3 * (size_t)hs[(size_t)(a * sv + l)] + d];
+          blo[d] = std::min(blo[d], x); bhi[d] = std::max(bhi[d], x);
+        }
+      int i0[3], i1[3];
+      for (int d = 0; d < 3; ++d) {
+        if (d >= dims) { i0[d] = i1[d] = 0; continue; }
+        i0[d] = std::max(0, (int)std::floor((blo[d] - lo[d]) / bh) - (blo[d] > lo[d] ? 0 : 0));
+        i1[d] = std::min(nb[d] - 1, (int)std::floor((bhi[d] - lo[d]) / bh));
+        if ((blo[d] - lo[d]) / bh - i0[d] < 1e-9 && i0[d] > 0) i0[d]--;
+        if (i1[d] < nb[d] - 1 && (i1[d] + 1) - (bhi[d] - lo[d]) / bh < 1e-9) i1[d]++;
+      }
+      for (int z = i0[2]; z <= i1[2]; ++z)
+        for (int y = i0[1]; y <= i1[1]; ++y)
+          for (int x = i0[0]; x <= i1[0]; ++x) bins[((size_t)z * nb[1] + y) * nb[0] + x].push_back((int)a);
+    }
+    std::vector<int> st(bins.size() + 1, 0), items;
+    for (size_t b = 0; b < bins.size(); ++b) {
+      st[b + 1] = st[b] + (int)bins[b].size();
+      items.insert(items.end(), bins[b].begin(), bins[b].end());
+    }
+    DALLOC(c->loc_start, int, st.size(), true);
+    DALLOC(c->loc_items, int, items.size() + 1, true);
+    CK(cudaMemcpy(c->loc_start, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!items.empty()) CK(cudaMemcpy(c->loc_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->L.start = c->loc_start; c->L.items = c->loc_items;
+    c->L.bx = nb[0]; c->L.by = nb[1]; c->L.bz = nb[2];
+    c->L.ox = lo[0]; c->L.oy = lo[1]; c->L.oz = lo[2]; c->L.ih = 1.0 / bh;
+  }
+  // site grid: the mesh box, padded; about 3.5 sites per cell in 3D, 2.5 in 2D and
+  // on surfaces (Sec. 5.2), sized from the mesh measure
+  {
+    double pad[3];
+    for (int d = 0; d < 3; ++d) pad[d] = 1e-3 * (hi[d] - lo[d]) + 1e-6;
+    double rho = mode == VD_MODE_3D ? 3.5 : 2.5;
+    double hh = mode == VD_MODE_3D ? std::cbrt(measure * rho / (double)c->n) : std::sqrt(measure * rho / (double)c->n);
+    double e[3];
+    for (int d = 0; d < 3; ++d) e[d] = hi[d] - lo[d] + 2 * pad[d];
+    for (;;) {
+      long long g[3];
+      for (int d = 0; d < 3; ++d) g[d] = std::max<long long>(1, (long long)std::ceil(e[d] / hh));
+      if (mode == VD_MODE_2D) g[2] = 1;
+      if (g[0] * g[1] * g[2] <= (1ll << 28)) {
+        c->gx = (int)g[0]; c->gy = (int)g[1]; c->gz = (int)g[2];
+        break;
+      }
+      hh *= 1.25;
+    }
+    c->h = hh;
+    c->ox = lo[0] - pad[0]; c->oy = lo[1] - pad[1]; c->oz = lo[2] - pad[2];
+    if (mode == VD_MODE_2D) { c->oz = -0.5 * hh; }
+    c->G = (long long)c->gx * c->gy * c->gz;
+  }
+  // per-computation buffers
+  long long n = c->n;
+  c->qcap = c->opt.queue_capacity > 0 ? c->opt.queue_capacity : 8 * (n + m) + 4096;
+  unsigned long long hc = 1;
+  while (hc < 2ull * (unsigned long long)c->qcap) hc <<= 1;
+  c->hmask = hc - 1;
+  c->fcap = 8 * c->qcap;
+  DALLOC(c->cellid, int, n, true);
+  DALLOC(c->ccount, int, c->G + 1, true);
+  DALLOC(c->cstart, int, c->G + 1, true);
+  DALLOC(c->ccur, int, c->G + 1, true);
+  {
+    char* p = nullptr;
+    rc = dalloc(c, p, (size_t)n * 4 * ts, true); if (rc) return rc; c->gs = p;
+    rc = dalloc(c, p, (size_t)n * ts, true); if (rc) return rc; c->delta = p;
+    rc = dalloc(c, p, (size_t)c->qcap * ts, true); if (rc) return rc; c->pmeas = p;
+    rc = dalloc(c, p, (size_t)c->qcap * 3 * ts, true); if (rc) return rc; c->pm1 = p;
+    rc = dalloc(c, p, (size_t)n * ts, true); if (rc) return rc; c->measure = p;
+    rc = dalloc(c, p, (size_t)n * 3 * ts, true); if (rc) return rc; c->centroid = p;
+  }
+  DALLOC(c->hash, unsigned long long, hc, true);
+  DALLOC(c->queue, unsigned long long, c->qcap, true);
+  DALLOC(c->ctr, unsigned long long, CTR_N, true);
+  DALLOC(c->pfoff, long long, c->qcap, true);
+  DALLOC(c->pfcnt, int, c->qcap + 1, true);
+  DALLOC(c->pflags, int, c->fcap, true);
+  DALLOC(c->scnt, int, n + 1, true);
+  DALLOC(c->soff, int, n + 1, true);
+  DALLOC(c->scur, int, n, true);
+  DALLOC(c->slist, int, c->qcap, true);
+  DALLOC(c->fc, int, n + 1, true);
+  DALLOC(c->foff, int, n + 1, true);
+  DALLOC(c->tmp, int, c->fcap, true);
+  DALLOC(c->ucnt, int, n + 1, true);
+  DALLOC(c->noff, long long, n + 1, true);
+  DALLOC(c->nidx, int, c->fcap, true);
+  {
+    long long L = std::max<long long>(c->G + 1, std::max<long long>(n + 1, c->qcap + 1));
+    long long* p = nullptr;
+    rc = dalloc(c, p, scan_tmp_elems(L), true); if (rc) return rc;
+    c->scan_tmp = p;
+  }
+  c->xs = c->xi = c->xflags = nullptr;
+  c->xoff = nullptr;
+  if (c->dtype == VD_F64) rc = flood_config<double, VD_MODE_2D>(c);
+  else if (mode == VD_MODE_3D) rc = flood_config<float, VD_MODE_3D>(c);
+  else if (mode == VD_MODE_SURFACE) rc = flood_config<float, VD_MODE_SURFACE>(c);
+  else rc = flood_config<float, VD_MODE_2D>(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_domain = true;
+  return VD_OK;
+}
+
+int vd_compute(vd_ctx* c, vd_result* out) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->have_domain) return VD_ERR_STATE;
+  CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
+  if (c->opt.timing && !c->ev[0])
+    for (int k = 0; k <= VD_PHASE_N; ++k) CK(cudaEventCreate(&c->ev[k]));
+  c->timing_now = c->opt.timing != 0;
+  enqueue_any(c);
+  CK(cudaGetLastError());
+  int st = read_status(c);
+  c->timing_now = false;
+  fill_result(c, out);
+  return st;
+}
+
+int vd_copy_result_host(vd_ctx* c, void* measure, void* centroid, int64_t* nbr_off, int32_t* nbr_idx) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->computed) return VD_ERR_STATE;
+  size_t ts = tsize(c->dtype);
+  if (measure) CK(cudaMemcpyAsync(measure, c->measure, (size_t)c->n * ts, cudaMemcpyDeviceToHost, c->stream));
+  if (centroid) CK(cudaMemcpyAsync(centroid, c->centroid, (size_t)c->n * 3 * ts, cudaMemcpyDeviceToHost, c->stream));
+  if (nbr_off) CK(cudaMemcpyAsync(nbr_off, c->noff, (size_t)(c->n + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (nbr_off && nbr_idx && c->last_nnz)
+    CK(cudaMemcpyAsync(nbr_idx, c->nidx, (size_t)c->last_nnz * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return VD_OK;
+}
+
+int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
+  if (!c || iters < 0) return VD_ERR_ARG;
+  if (!c->have_domain) return VD_ERR_STATE;
+  if (iters == 0) return VD_OK;
+  CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
+  if (use_graph) {
+    if (!c->gexec) {
+      cudaStream_t cap = c->stream;
+      if (!cap) {
+        if (!c->own_stream) CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+        cap = c->own_stream;
+      }
+      cudaStream_t saved = c->stream;
+      CK(cudaStreamSynchronize(saved));
+      c->stream = cap;
+      CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      enqueue_any(c);
+      enqueue_lloyd(c);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cap, &g);
+      c->stream = saved;
+      if (e != cudaSuccess) return VD_ERR_CUDA;
+      c->graph = g;
+      CK(cudaGraphInstantiate(&c->gexec, g, 0));
+    }
+    cudaStream_t run = c->stream ? c->stream : c->own_stream;
+    if (run != c->stream) { CK(cudaStreamSynchronize(c->stream)); }
+    for (int t = 0; t < iters; ++t) CK(cudaGraphLaunch(c->gexec, run));
+    if (run != c->stream) { CK(cudaStreamSynchronize(run)); }
+  } else {
+    for (int t = 0; t < iters; ++t) {
+      enqueue_any(c);
+      enqueue_lloyd(c);
+    }
+  }
+  CK(cudaGetLastError());
+  return read_status(c);
+}
+
+int vd_get_pieces(vd_ctx* c, vd_pieces* out) {
+  if (!c || !out) return VD_ERR_ARG;
+  if (!c->computed) return VD_ERR_STATE;
+  long long np = c->last_pairs;
+  if (!c->xs) {
+    DALLOC(c->xs, int, c->qcap, true);
+    DALLOC(c->xi, int, c->qcap, true);
+    DALLOC(c->xoff, long long, c->qcap + 1, true);
+    DALLOC(c->xflags, int, c->fcap, true);
+  }
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(c->pfcnt + np, 0, sizeof(int), s));
+  if (c->dtype == VD_F64) {
+    Dev<double> D = make_dev<double>(c);
+    k_export_ids<double><<<c->nsm * 8, 256, 0, s>>>(D, c->xs, c->xi);
+    scan_excl<int, long long>(s, c->pfcnt, c->xoff, np + 1, (long long*)c->scan_tmp);
+    k_export_flags<double><<<c->nsm * 8, 256, 0, s>>>(D, c->xoff, c->xflags);
+  } else {
+    Dev<float> D = make_dev<float>(c);
+    k_export_ids<float><<<c->nsm * 8, 256, 0, s>>>(D, c->xs, c->xi);
+    scan_excl<int, long long>(s, c->pfcnt, c->xoff, np + 1, (long long*)c->scan_tmp);
+    k_export_flags<float><<<c->nsm * 8, 256, 0, s>>>(D, c->xoff, c->xflags);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  out->n_pieces = np;
+  out->simplex = c->xs;
+  out->site = c->xi;
+  out->measure = c->pmeas;
+  out->moment = c->pm1;
+  out->flag_off = (const int64_t*)c->xoff;
+  out->flags = c->xflags;
+  return VD_OK;
+}
+
+int vd_set_candidates(vd_ctx* c, const int32_t* cand, int k) {
+  if (!c || k < 0 || (k > 0 && !cand)) return VD_ERR_ARG;
+  if (c->cand) {
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)c->cand);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(c->cand);
+    c->cand = nullptr;
+  }
+  c->ncand = k;
+  if (k == 0) return VD_OK;
+  int* p = nullptr;
+  int rc = dalloc(c, p, (size_t)c->n * k, false);
+  if (rc) return rc;
+  c->cand = p;
+  CK(cudaMemcpyAsync(p, cand, (size_t)c->n * k * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  return VD_OK;
+}
+
+void vd_destroy(vd_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_domain(c);
+  for (void* p : c->allocs) cudaFree(p);
+  for (int k = 0; k <= VD_PHASE_N; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+}  // extern "C"

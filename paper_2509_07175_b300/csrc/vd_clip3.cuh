@@ -1,0 +1,610 @@
+// vd_clip3.cuh -- tetrahedron / Voronoi-cell intersection, one warp per pair.
+//
+// The working polytope P (Sec. 5.3) is kept as a triangulated dual mesh in the
+// warp's shared memory: each plane (tet face or bisector) is a dual vertex,
+// each corner of P -- the meeting point of three planes -- is a dual triangle,
+// stored with its three neighbours.  Clipping by a bisector removes the
+// connected set R_p of outside corners that contains the chosen outside corner
+// p, walks the boundary of R_p and fans new corners to the new plane
+// (Sec. 5.3).  Alg. 3 drives the clipping: while a corner p lies outside
+// Omega_i, find a bisector on the virtual edge v_i -> p (Sec. 3.2, improved
+// start point of Sec. 5.1) and clip by it.
+//
+// Geometry is FP32 in the frame of v_i.  Every corner carries a bound on the
+// error of its coordinates; side tests that do not clear their bound are
+// settled by the float64 predicate on the defining planes (vd_common.cuh).
+#pragma once
+
+#include "vd_dev.cuh"
+
+namespace vd {
+namespace c3 {
+
+constexpr int MAXP = 48;   // planes
+constexpr int MAXT = 96;   // corners (3 x 32 slots)
+constexpr float U = 5.9604644775390625e-8f;
+constexpr float GAMMA = 64.f * U;   // corner error factor (see corner())
+constexpr float SIDEF = 24.f * U;   // side-test error factor
+
+struct Warp3 {
+  float4 pn[MAXP];      // n.xyz, c : inside is n.x <= c
+  float2 pm[MAXP];      // magnitudes: |n~|_1 and c~ (absolute-value evaluation)
+  int psrc[MAXP];       // >= 0: bisector with that site; -1-f: face f of the tetrahedron
+  uchar4 tv[MAXT];      // the corner's planes x, y, z (dual triangle, oriented)
+  uchar4 tn[MAXT];      // neighbour corners across dual edges x->y, y->z, z->x
+  float4 tq[MAXT];      // corner coordinates (frame of v_i), w = coordinate error bound
+  int twit[MAXT];       // certified closer site of an outside corner
+  int stri[MAXP], etri[MAXP];  // boundary loop: new corner starting / ending at a plane
+  int pref[MAXP];       // reference corner of each face (integration)
+  float parea[MAXP][3]; // face vector areas
+  ScanScratch S;
+  CornerScratch A;
+};
+
+// warp-uniform bookkeeping (identical in every lane)
+struct Masks {
+  unsigned alive[3], in[3], out[3];
+  unsigned long long palive;
+};
+
+__device__ __forceinline__ bool bit(const unsigned* m, int t) { return (m[t >> 5] >> (t & 31)) & 1u; }
+
+__device__ __forceinline__ int nth_set(unsigned m, int k) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w; w >>= 1) {
+    unsigned lo = m & ((1u << w) - 1u);
+    int c = __popc(lo);
+    if (k >= c) { k -= c; m >>= w; pos += w; } else m = lo;
+  }
+  return pos;
+}
+
+// ----- planes --------------------------------------------------------------
+// tet face f: the plane through the three vertices other than f, oriented by
+// fsgn so that its normal points away from vertex f
+__device__ __forceinline__ void face_verts(int f, int& a0, int& a1, int& a2) {
+  a0 = f == 0 ? 1 : 0;
+  a1 = f <= 1 ? 2 : 1;
+  a2 = f <= 2 ? 3 : 2;
+}
+
+__device__ void plane_face(const Dev<float>& C, int a, int f, float3 vi, float4& P, float2& M) {
+  int l0, l1, l2;
+  face_verts(f, l0, l1, l2);
+  const int* s = C.simp + 4 * a;
+  const float* A = C.verts + 3 * s[l0];
+  const float* B = C.verts + 3 * s[l1];
+  const float* Cc = C.verts + 3 * s[l2];
+  float sg = (float)C.fsgn[4 * a + f];
+  float e1x = B[0] - A[0], e1y = B[1] - A[1], e1z = B[2] - A[2];
+  float e2x = Cc[0] - A[0], e2y = Cc[1] - A[1], e2z = Cc[2] - A[2];
+  float nx = sg * (e1y * e2z - e1z * e2y), ny = sg * (e1z * e2x - e1x * e2z), nz = sg * (e1x * e2y - e1y * e2x);
+  float ax = A[0] - vi.x, ay = A[1] - vi.y, az = A[2] - vi.z;
+  float mx = fabsf(e1y * e2z) + fabsf(e1z * e2y), my = fabsf(e1z * e2x) + fabsf(e1x * e2z),
+        mz = fabsf(e1x * e2y) + fabsf(e1y * e2x);
+  P = make_float4(nx, ny, nz, nx * ax + ny * ay + nz * az);
+  M = make_float2(mx + my + mz, mx * fabsf(ax) + my * fabsf(ay) + mz * fabsf(az));
+}
+
+__device__ __forceinline__ void plane_bis(const Dev<float>& C, int j, float3 vi, float4& P, float2& M) {
+  float wx = C.sites[3 * j] - vi.x, wy = C.sites[3 * j + 1] - vi.y, wz = C.sites[3 * j + 2] - vi.z;
+  float c = 0.5f * (wx * wx + wy * wy + wz * wz);
+  P = make_float4(wx, wy, wz, c);
+  M = make_float2(fabsf(wx) + fabsf(wy) + fabsf(wz), c);
+}
+
+// float64 plane from its source, with running error bounds
+__device__ ePlane eplane(const Dev<float>& C, int a, int i, int src) {
+  ed3 vi{mk(C.sites[3 * i]), mk(C.sites[3 * i + 1]), mk(C.sites[3 * i + 2])};
+  ePlane p;
+  if (src >= 0) {
+    ed3 vj{mk(C.sites[3 * src]), mk(C.sites[3 * src + 1]), mk(C.sites[3 * src + 2])};
+    p.n = sub3(vj, vi);
+    p.c = half(dot3(p.n, p.n));
+    return p;
+  }
+  int f = -1 - src, l0, l1, l2;
+  face_verts(f, l0, l1, l2);
+  const int* s = C.simp + 4 * a;
+  const float* A = C.verts + 3 * s[l0];
+  const float* B = C.verts + 3 * s[l1];
+  const float* Cc = C.verts + 3 * s[l2];
+  ed3 eA{mk(A[0]), mk(A[1]), mk(A[2])}, eB{mk(B[0]), mk(B[1]), mk(B[2])}, eC{mk(Cc[0]), mk(Cc[1]), mk(Cc[2])};
+  p.n = scale3(cross3(sub3(eB, eA), sub3(eC, eA)), (double)C.fsgn[4 * a + f]);
+  p.c = dot3(p.n, sub3(eA, vi));
+  return p;
+}
+
+// ----- corners ---------------------------------------------------------------
+// Corner of three planes by Cramer's rule.  With D = det N and A = adj(N) c,
+// |D^ - D| <= g D~ and |A^ - A| <= g A~, where ~ is the same expression on
+// absolute values (bounded here by products of the planes' magnitudes) and g
+// covers the rounding of the plane coefficients and of the evaluation; then
+// |q^ - q| <= (g A~ + |q| g D~) / (|D^| - g D~) + 2u|q|.  Corners whose D does
+// not clear its bound get an infinite error: every test on them is exact.
+__device__ float4 corner(float4 P0, float2 M0, float4 P1, float2 M1, float4 P2, float2 M2) {
+  float3 x12 = make_float3(P1.y * P2.z - P1.z * P2.y, P1.z * P2.x - P1.x * P2.z, P1.x * P2.y - P1.y * P2.x);
+  float3 x20 = make_float3(P2.y * P0.z - P2.z * P0.y, P2.z * P0.x - P2.x * P0.z, P2.x * P0.y - P2.y * P0.x);
+  float3 x01 = make_float3(P0.y * P1.z - P0.z * P1.y, P0.z * P1.x - P0.x * P1.z, P0.x * P1.y - P0.y * P1.x);
+  float D = P0.x * x12.x + P0.y * x12.y + P0.z * x12.z;
+  float qx = (P0.w * x12.x + P1.w * x20.x + P2.w * x01.x) / D;
+  float qy = (P0.w * x12.y + P1.w * x20.y + P2.w * x01.y) / D;
+  float qz = (P0.w * x12.z + P1.w * x20.z + P2.w * x01.z) / D;
+  float Dm = M0.x * M1.x * M2.x;
+  float Am = M0.y * M1.x * M2.x + M1.y * M2.x * M0.x + M2.y * M0.x * M1.x;
+  float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+  float den = fabsf(D) - GAMMA * Dm;
+  float e = (den > GAMMA * Dm && isfinite(qm)) ? (GAMMA * Am + qm * GAMMA * Dm) / den + 2.f * U * qm : 1e30f;
+  return make_float4(qx, qy, qz, e);
+}
+
+// ----- exact side tests ----------------------------------------------------------
+__device__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4) {
+  ePlane p[4];
+  uchar4 v = W.tv[t];
+  // the corner lies on each of its own planes: the side value is exactly zero
+  if (src4 == W.psrc[v.x] || src4 == W.psrc[v.y] || src4 == W.psrc[v.z]) return 0;
+  p[0] = eplane(C, a, i, W.psrc[v.x]);
+  p[1] = eplane(C, a, i, W.psrc[v.y]);
+  p[2] = eplane(C, a, i, W.psrc[v.z]);
+  p[3] = eplane(C, a, i, src4);
+  int certain, tie;
+  int s = side_from_planes(p, &certain, &tie);
+  atomicAdd(C.stats + VD_STAT_FP64, 1ull);
+  if (!certain) {
+    atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
+    record_diag(C.stats, a, i, W.psrc[v.x], W.psrc[v.y], W.psrc[v.z], src4, tie, 0);
+  }
+  return s;
+}
+
+// side of corner t w.r.t. plane P (slot pl): -1 outside, +1 inside, 0 tie (inside)
+__device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int a, int i, int t, int pl) {
+  float4 q = W.tq[t];
+  float4 P = W.pn[pl];
+  float2 M = W.pm[pl];
+  if (q.w < 1e29f) {
+    float s = P.w - (P.x * q.x + P.y * q.y + P.z * q.z);
+    float qm = fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z)));
+    float b = (fabsf(P.x) + fabsf(P.y) + fabsf(P.z)) * q.w + SIDEF * (M.y + M.x * qm);
+    if (s > b) return 1;
+    if (s < -b) return -1;
+  }
+  return exact_side(C, W, a, i, t, W.psrc[pl]);
+}
+
+// ----- one pair ------------------------------------------------------------------
+struct Counters {
+  unsigned long long nn, corner, clips, lam, search, scanned, learned, fallback;
+};
+
+__device__ __forceinline__ void add_plane(Warp3& W, int slot, float4 P, float2 M, int src, int lane) {
+  __syncwarp();
+  if (lane == 0) { W.pn[slot] = P; W.pm[slot] = M; W.psrc[slot] = src; }
+  __syncwarp();
+}
+
+// nearest site through the warp (counted)
+__device__ __forceinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, float y, float z, int lane,
+                                        Counters& K) {
+  float d2;
+  int sc = 0;
+  int k = warp_nearest(C.G, x, y, z, lane, W.S, d2, &sc);
+  K.nn++;
+  K.scanned += sc;
+  return k;
+}
+
+// Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
+// Returns the bisector site j for the outside corner t.
+__device__ int find_bisector(const Dev<float>& C, Warp3& W, int i, float3 vi, int t, int lane, Counters& K) {
+  float4 q = W.tq[t];
+  int wit = W.twit[t];
+  float dist = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
+  float dx = q.x / dist, dy = q.y / dist, dz = q.z / dist;
+  float gx = q.x, gy = q.y, gz = q.z;
+  int j = wit;
+  float delta = C.delta[i];
+  for (int lam = 2; lam < 2 + C.max_lambda; ++lam) {
+    float step = (float)lam * delta;
+    if (!(step < dist)) break;
+    float sx = dx * step, sy = dy * step, sz = dz * step;
+    int k = nn_query(C, W, vi.x + sx, vi.y + sy, vi.z + sz, lane, K);
+    K.lam++;
+    if (k != i) { gx = sx; gy = sy; gz = sz; j = k; break; }
+  }
+  for (int s = 0; s < C.max_search; ++s) {
+    float wx = C.sites[3 * j] - vi.x, wy = C.sites[3 * j + 1] - vi.y, wz = C.sites[3 * j + 2] - vi.z;
+    float den = wx * gx + wy * gy + wz * gz;
+    if (!(den > 0.f)) { K.fallback++; return wit; }
+    float tt = 0.5f * (wx * wx + wy * wy + wz * wz) / den;
+    if (!(tt < 1.f)) return j;   // the bisector meets the segment at its end
+    float sx = gx * tt, sy = gy * tt, sz = gz * tt;
+    int k = nn_query(C, W, vi.x + sx, vi.y + sy, vi.z + sz, lane, K);
+    K.search++;
+    if (k == i || k == j) return j;
+    j = k;
+    gx = sx; gy = sy; gz = sz;
+  }
+  K.fallback++;
+  return wit;
+}
+
+// Clip by the plane in slot pl, removing the component of outside corners that
+// contains p.  Returns 0 (clipped), 1 (P became empty), -1 (error, status set).
+__device__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, int pl, int p, int lane) {
+  unsigned om[3], R[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    bool o = bit(Mk.alive, t) && side_of(C, W, a, i, t, pl) < 0;
+    om[r] = __ballot_sync(FULL, o);
+    R[r] = 0;
+  }
+  if (!bit(om, p)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
+  R[p >> 5] = 1u << (p & 31);
+  for (int it = 0; it < MAXT; ++it) {
+    unsigned nR[3];
+    bool ch = false;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      int t = r * 32 + lane;
+      bool add = false;
+      if (bit(om, t) && !bit(R, t)) {
+        uchar4 nb = W.tn[t];
+        add = bit(R, nb.x) || bit(R, nb.y) || bit(R, nb.z);
+      }
+      nR[r] = R[r] | __ballot_sync(FULL, add);
+      ch |= nR[r] != R[r];
+    }
+    R[0] = nR[0]; R[1] = nR[1]; R[2] = nR[2];
+    if (!ch) break;
+  }
+  if (R[0] == Mk.alive[0] && R[1] == Mk.alive[1] && R[2] == Mk.alive[2]) return 1;
+  // boundary edges of R: (x -> y) of a removed corner whose neighbour u is kept
+  int cnt[3];
+  int ex[3][3], ey[3][3], eu[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    cnt[r] = 0;
+    if (bit(R, t)) {
+      uchar4 v = W.tv[t], nb = W.tn[t];
+      int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+        if (!bit(R, nn[e])) { ex[r][cnt[r]] = vv[e]; ey[r][cnt[r]] = vv[(e + 1) % 3]; eu[r][cnt[r]] = nn[e]; cnt[r]++; }
+    }
+  }
+  unsigned fr[3] = {~Mk.alive[0] | R[0], ~Mk.alive[1] | R[1], ~Mk.alive[2] | R[2]};
+  int nfree = __popc(fr[0]) + __popc(fr[1]) + __popc(fr[2]);
+  int base[3], total = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int inc = warp_incl_scan(cnt[r], lane);
+    base[r] = total + inc - cnt[r];
+    total += __shfl_sync(FULL, inc, 31);
+  }
+  if (total > nfree || total < 3) { set_error(C.status, total < 3 ? VD_ERR_LIMIT : VD_ERR_CAPACITY); return -1; }
+  // reset the loop maps, then claim them
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < cnt[r]; ++c) { W.stri[ex[r][c]] = -1; W.etri[ey[r][c]] = -1; }
+  __syncwarp();
+  int slot[3][3];
+  bool bad = false;
+  unsigned newm[3] = {0, 0, 0};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < cnt[r]; ++c) {
+      int k = base[r] + c;
+      int c0 = __popc(fr[0]), c1 = __popc(fr[1]);
+      int s = k < c0 ? nth_set(fr[0], k) : (k < c0 + c1 ? 32 + nth_set(fr[1], k - c0) : 64 + nth_set(fr[2], k - c0 - c1));
+      slot[r][c] = s;
+      if (atomicExch(&W.stri[ex[r][c]], s) != -1) bad = true;
+      if (atomicExch(&W.etri[ey[r][c]], s) != -1) bad = true;
+    }
+  if (__any_sync(FULL, bad)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
+  __syncwarp();
+  // write the new corners (their slots held removed corners or were free)
+  float4 Pn = W.pn[pl];
+  float2 Mn = W.pm[pl];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < cnt[r]; ++c) {
+      int s = slot[r][c], x = ex[r][c], y = ey[r][c], u = eu[r][c];
+      W.tv[s] = make_uchar4((unsigned char)x, (unsigned char)y, (unsigned char)pl, 0);
+      W.tn[s] = make_uchar4((unsigned char)u, (unsigned char)W.stri[y], (unsigned char)W.etri[x], 0);
+      uchar4 uv = W.tv[u];
+      if (uv.x == y && uv.y == x) W.tn[u].x = (unsigned char)s;
+      else if (uv.y == y && uv.z == x) W.tn[u].y = (unsigned char)s;
+      else if (uv.z == y && uv.x == x) W.tn[u].z = (unsigned char)s;
+      else bad = true;
+      float4 qc = corner(W.pn[x], W.pm[x], W.pn[y], W.pm[y], Pn, Mn);
+      if (!(qc.w <= 3e-3f * sqrtf(qc.x * qc.x + qc.y * qc.y + qc.z * qc.z))) {
+        // loose FP32 bound: recompute the corner from its exact planes in float64
+        qc = corner64(eplane(C, a, i, W.psrc[x]), eplane(C, a, i, W.psrc[y]), eplane(C, a, i, W.psrc[pl]));
+        atomicAdd(C.stats + VD_STAT_FP64, 1ull);
+      }
+      W.tq[s] = qc;
+      W.twit[s] = -1;
+      newm[s >> 5] |= 1u << (s & 31);
+    }
+  __syncwarp();
+  if (__any_sync(FULL, bad)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    unsigned nm = __reduce_or_sync(FULL, newm[r]);
+    Mk.alive[r] = (Mk.alive[r] & ~R[r]) | nm;
+    Mk.in[r] &= ~(R[r] | nm);
+    Mk.out[r] &= ~(R[r] | nm);
+  }
+  // planes still referenced by a corner
+  unsigned long long pm = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    if (bit(Mk.alive, t)) {
+      uchar4 v = W.tv[t];
+      pm |= (1ull << v.x) | (1ull << v.y) | (1ull << v.z);
+    }
+  }
+  unsigned lo = __reduce_or_sync(FULL, (unsigned)pm), hi = __reduce_or_sync(FULL, (unsigned)(pm >> 32));
+  Mk.palive = ((unsigned long long)hi << 32) | lo;
+  __syncwarp();
+  return 0;
+}
+
+#ifdef VD_CHECK
+// Consistency of the dual mesh after a clip (checking builds only): neighbours
+// are mutual, and no corner is certifiably outside an alive plane.
+__device__ void check_mesh(const Dev<float>& C, Warp3& W, const Masks& Mk, int a, int i, int pl_new, int lane) {
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    if (!bit(Mk.alive, t)) continue;
+    uchar4 v = W.tv[t], nb = W.tn[t];
+    int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
+    for (int e = 0; e < 3; ++e) {
+      int u = nn[e], x = vv[e], y = vv[(e + 1) % 3];
+      uchar4 uv = W.tv[u], un = W.tn[u];
+      int back = (uv.x == y && uv.y == x) ? un.x : (uv.y == y && uv.z == x) ? un.y : (uv.z == y && uv.x == x) ? un.z : -1;
+      if (!bit(Mk.alive, u) || back != t) {
+        set_error(C.status, VD_ERR_LIMIT);
+        record_diag(C.stats, a, i, t, u, x, y, back, 2);
+      }
+    }
+    for (int x = 0; x < MAXP; ++x) {
+      if (!((Mk.palive >> x) & 1ull) || x == v.x || x == v.y || x == v.z) continue;
+      float4 q = W.tq[t], P = W.pn[x];
+      float2 M = W.pm[x];
+      float sd = P.w - (P.x * q.x + P.y * q.y + P.z * q.z);
+      float qm = fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z)));
+      float b = (fabsf(P.x) + fabsf(P.y) + fabsf(P.z)) * q.w + SIDEF * (M.y + M.x * qm);
+      if (sd < -b) {
+        set_error(C.status, VD_ERR_LIMIT);
+        record_diag(C.stats, a, i, t, x, W.psrc[x], pl_new, __float_as_int(q.w), 3);
+      }
+    }
+  }
+  __syncwarp();
+}
+#endif
+
+// Integrate volume, first moment (frame of v_i) and face areas of the current
+// polytope; sigma is +-1 (orientation of the dual mesh against space).
+__device__ void integrate(Warp3& W, const Masks& Mk, float sigma, int lane, float& vol, float3& m1) {
+  for (int x = lane; x < MAXP; x += 32) {
+    W.pref[x] = 0x7fffffff;
+    W.parea[x][0] = W.parea[x][1] = W.parea[x][2] = 0.f;
+  }
+  __syncwarp();
+  int o = -1;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    if (bit(Mk.alive, t)) {
+      uchar4 v = W.tv[t];
+      atomicMin(&W.pref[v.x], t); atomicMin(&W.pref[v.y], t); atomicMin(&W.pref[v.z], t);
+    }
+    unsigned m = Mk.alive[r];
+    if (o < 0 && m) o = r * 32 + __ffs(m) - 1;
+  }
+  __syncwarp();
+  float4 O = W.tq[o];
+  float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    if (!bit(Mk.alive, t)) continue;
+    uchar4 v = W.tv[t], nb = W.tn[t];
+    int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
+    float4 A4 = W.tq[t];
+    float ax = A4.x - O.x, ay = A4.y - O.y, az = A4.z - O.z;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      int x = vv[e];
+      float4 R4 = W.tq[W.pref[x]], B4 = W.tq[nn[e]];
+      float rx = R4.x - O.x, ry = R4.y - O.y, rz = R4.z - O.z;
+      float bx = B4.x - O.x, by = B4.y - O.y, bz = B4.z - O.z;
+      float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+      float det = rx * cx + ry * cy + rz * cz;
+      v6 += det;
+      mx += det * (rx + ax + bx);
+      my += det * (ry + ay + by);
+      mz += det * (rz + az + bz);
+      float ux = ax - rx, uy = ay - ry, uz = az - rz, wx = bx - rx, wy = by - ry, wz = bz - rz;
+      atomicAdd(&W.parea[x][0], uy * wz - uz * wy);
+      atomicAdd(&W.parea[x][1], uz * wx - ux * wz);
+      atomicAdd(&W.parea[x][2], ux * wy - uy * wx);
+    }
+  }
+  v6 = warp_sum(v6);
+  mx = warp_sum(mx); my = warp_sum(my); mz = warp_sum(mz);
+  vol = sigma * v6 / 6.f;
+  float s24 = sigma / 24.f;
+  m1 = make_float3(s24 * mx + vol * O.x, s24 * my + vol * O.y, s24 * mz + vol * O.z);
+  __syncwarp();
+}
+
+// the corner table of a tetrahedron: corner k (vertex k) is where the three faces
+// other than f = k meet; dual triangles oriented as the boundary of a simplex
+__constant__ unsigned char TET_TV[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+
+__device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, float3 vi, int lane) {
+  if (lane < 4) {
+    float4 P;
+    float2 M;
+    plane_face(C, a, lane, vi, P, M);
+    W.pn[lane] = P; W.pm[lane] = M; W.psrc[lane] = -1 - lane;
+    int k = lane;
+    const float* V = C.verts + 3 * C.simp[4 * a + k];
+    float qx = V[0] - vi.x, qy = V[1] - vi.y, qz = V[2] - vi.z;
+    float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+    W.tq[k] = make_float4(qx, qy, qz, 2.f * U * qm);
+    unsigned char x = TET_TV[k][0], y = TET_TV[k][1], z = TET_TV[k][2];
+    W.tv[k] = make_uchar4(x, y, z, 0);
+    // across dual edge (x,y) lies the corner at the tet vertex that is neither k, x nor y
+    unsigned char n0 = (unsigned char)(6 - k - x - y), n1 = (unsigned char)(6 - k - y - z),
+                  n2 = (unsigned char)(6 - k - z - x);
+    W.tn[k] = make_uchar4(n0, n1, n2, 0);
+    W.twit[k] = -1;
+  }
+  Mk.alive[0] = 0xFu; Mk.alive[1] = Mk.alive[2] = 0;
+  Mk.in[0] = Mk.in[1] = Mk.in[2] = 0;
+  Mk.out[0] = Mk.out[1] = Mk.out[2] = 0;
+  Mk.palive = 0xFull;
+  __syncwarp();
+}
+
+__device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long long slot, int lane) {
+  Counters K = {0, 0, 0, 0, 0, 0, 0, 0};
+  float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
+  Masks Mk;
+  init_tet(C, W, Mk, a, i, vi, lane);
+  float sigma;
+  {
+    float v0;
+    float3 m0;
+    integrate(W, Mk, 1.f, lane, v0, m0);
+    sigma = v0 < 0.f ? -1.f : 1.f;
+  }
+  bool empty = false;
+  int nclip = 0;
+  for (;;) {
+    // first corner (in slot order) outside Omega_i; each corner is tested once
+    int p = -1;
+    for (;;) {
+      unsigned c0 = Mk.alive[0] & ~Mk.in[0], c1 = Mk.alive[1] & ~Mk.in[1], c2 = Mk.alive[2] & ~Mk.in[2];
+      int t = c0 ? __ffs(c0) - 1 : (c1 ? 31 + __ffs(c1) : (c2 ? 63 + __ffs(c2) : -1));
+      if (t < 0) break;
+      if (bit(Mk.out, t)) { p = t; break; }
+      float4 q = W.tq[t];
+      uchar4 v = W.tv[t];
+      int ex[3];
+      ex[0] = W.psrc[v.x]; ex[1] = W.psrc[v.y]; ex[2] = W.psrc[v.z];
+      for (int u = 0; u < 3; ++u) if (ex[u] < 0) ex[u] = -2;  // tet faces exclude no site
+      auto exact = [&](int k) { return exact_side(C, W, a, i, t, k); };
+      int wit;
+      int sc = 0;
+      int out = corner_outside(C, i, vi.x, vi.y, vi.z, q.x, q.y, q.z, q.w, ex, lane, W.S, W.A, exact, &wit, &sc);
+      K.corner++;
+      K.nn++;
+      K.scanned += sc;
+      if (*(volatile int*)C.status) return;
+      if (out) {
+        Mk.out[t >> 5] |= 1u << (t & 31);
+        if (lane == 0) W.twit[t] = wit;
+        __syncwarp();
+        p = t;
+        break;
+      }
+      Mk.in[t >> 5] |= 1u << (t & 31);
+    }
+    if (p < 0) break;
+    if (++nclip > C.max_clips) { set_error(C.status, VD_ERR_LIMIT); return; }
+    int j = find_bisector(C, W, i, vi, p, lane, K);
+    // free plane slot for B_ij
+    unsigned long long freep = ~Mk.palive & ((1ull << MAXP) - 1ull);
+    if (!freep) { set_error(C.status, VD_ERR_CAPACITY); return; }
+    int pl = __ffsll((long long)freep) - 1;
+    float4 P;
+    float2 M;
+    plane_bis(C, j, vi, P, M);
+    add_plane(W, pl, P, M, j, lane);
+    if (side_of(C, W, a, i, p, pl) >= 0) {
+      // FP32 search landed on a bisector that does not cut p: use the certified closer site
+      K.fallback++;
+      j = W.twit[p];
+      plane_bis(C, j, vi, P, M);
+      add_plane(W, pl, P, M, j, lane);
+    }
+    int rc = clip(C, W, Mk, a, i, pl, p, lane);
+    K.clips++;
+    if (rc < 0) return;
+#ifdef VD_CHECK
+    if (rc == 0) check_mesh(C, W, Mk, a, i, pl, lane);
+#endif
+    if (rc == 1) { empty = true; break; }
+  }
+  float vol = 0.f;
+  float3 m1 = make_float3(0.f, 0.f, 0.f);
+  if (!empty) integrate(W, Mk, sigma, lane, vol, m1);
+  bool nonempty = !empty && vol > 0.f;
+  // faces of positive area: output flags and propagate (Alg. 4 / Alg. 5 rules)
+  int nflag = 0;
+  int myflag[2];
+  bool has[2] = {false, false};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int x = lane + 32 * h;
+    if (nonempty && x < MAXP && ((Mk.palive >> x) & 1ull)) {
+      float ax = W.parea[x][0], ay = W.parea[x][1], az = W.parea[x][2];
+      if (ax * ax + ay * ay + az * az > 0.f) {
+        int src = W.psrc[x];
+        if (src >= 0) {
+          myflag[h] = src;
+          push_pair(C, a, src);
+        } else {
+          int b = C.adj[4 * a + (-1 - src)];
+          myflag[h] = b >= 0 ? -(b + 1) : FLAG_BOUNDARY;
+          if (b >= 0) push_pair(C, b, i);
+        }
+        has[h] = true;
+      }
+    }
+  }
+  unsigned b0 = __ballot_sync(FULL, has[0]), b1 = __ballot_sync(FULL, has[1]);
+  nflag = __popc(b0) + __popc(b1);
+  long long fbase = 0;
+  if (lane == 0 && nflag) fbase = (long long)atomicAdd(C.ctr + CTR_FLAGS, (unsigned long long)nflag);
+  fbase = __shfl_sync(FULL, fbase, 0);
+  if (fbase + nflag > C.fcap) { set_error(C.status, VD_ERR_CAPACITY); return; }
+  unsigned lt = (1u << lane) - 1u;
+  if (has[0]) C.pflags[fbase + __popc(b0 & lt)] = myflag[0];
+  if (has[1]) C.pflags[fbase + __popc(b0) + __popc(b1 & lt)] = myflag[1];
+  if (lane == 0) {
+    C.pmeas[slot] = nonempty ? vol : 0.f;
+    C.pm1[3 * slot] = nonempty ? m1.x : 0.f;
+    C.pm1[3 * slot + 1] = nonempty ? m1.y : 0.f;
+    C.pm1[3 * slot + 2] = nonempty ? m1.z : 0.f;
+    C.pfoff[slot] = fbase;
+    C.pfcnt[slot] = nflag;
+    if (C.want_stats) {
+      stat_add(C, VD_STAT_NN_QUERIES, K.nn);
+      stat_add(C, VD_STAT_CORNER_TESTS, K.corner);
+      stat_add(C, VD_STAT_CLIPS, K.clips);
+      stat_add(C, VD_STAT_LAMBDA_STEPS, K.lam);
+      stat_add(C, VD_STAT_SEARCH_STEPS, K.search);
+      stat_add(C, VD_STAT_SITES_SCANNED, K.scanned);
+      stat_add(C, VD_STAT_FALLBACK, K.fallback);
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace c3
+}  // namespace vd

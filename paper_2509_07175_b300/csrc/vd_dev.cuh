@@ -1,0 +1,184 @@
+// vd_dev.cuh -- device context, (simplex, site) pair set and work queue, and
+// the certified point-in-cell test on polytope corners (Sec. 3.1).
+#pragma once
+
+#include "vd_grid.cuh"
+
+namespace vd {
+
+// counters in Dev::ctr
+enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_N = 8 };
+
+template <typename T>
+struct Dev {
+  int mode;              // VD_MODE_*
+  int n, m, k;           // sites, simplices, vertices per simplex
+  const T* sites;        // [n*3] original order (z = 0 in 2D)
+  const T* verts;        // [nv*3]
+  const int* simp;       // [m*k]
+  const int* adj;        // [m*k] neighbour across the face opposite local vertex f, -1: boundary
+  const signed char* fsgn;  // [m*k] +-1: orientation making the face normal point outward
+  const T* delta;        // [n] half the distance to the nearest other site (Sec. 5.1)
+  GridView<T> G;
+  // learned proposal
+  const int* cand;       // [n*ncand] candidate neighbours, -1 unused
+  int ncand;
+  // pair set and queue
+  unsigned long long* hash;
+  unsigned long long hmask;
+  unsigned long long* queue;
+  long long qcap;
+  unsigned long long* ctr;  // CTR_*
+  // per queue slot output
+  T* pmeas;
+  T* pm1;                // [qcap*3] first moment, frame of the site
+  long long* pfoff;      // start of the slot's flags in pflags
+  int* pfcnt;            // number of flags
+  int* pflags;
+  long long fcap;
+  // status
+  int* status;
+  unsigned long long* stats;  // [VD_STAT_N]
+  int want_stats;
+  int max_clips, max_search, max_lambda;
+  long long wait_ns;
+};
+
+__device__ __forceinline__ unsigned long long pair_key(int a, int i) {
+  return ((unsigned long long)(unsigned)a << 32) | (unsigned)i;
+}
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30; x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27; x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+// Insert (a,i) into the pair set ("label it in atomic", Alg. 4); a new pair is
+// appended to the queue.  Returns 1 if new.
+template <typename T>
+__device__ int push_pair(const Dev<T>& C, int a, int i) {
+  unsigned long long key = pair_key(a, i);
+  unsigned long long h = mix64(key) & C.hmask;
+  for (unsigned long long probe = 0; probe <= C.hmask; ++probe) {
+    unsigned long long prev = atomicCAS(C.hash + h, EMPTY_KEY, key);
+    if (prev == key) return 0;
+    if (prev == EMPTY_KEY) {
+      unsigned long long pos = atomicAdd(C.ctr + CTR_TAIL, 1ull);
+      if ((long long)pos >= C.qcap) { set_error(C.status, VD_ERR_CAPACITY); return 0; }
+      C.queue[pos] = key;
+      __threadfence();
+      return 1;
+    }
+    h = (h + 1) & C.hmask;
+  }
+  set_error(C.status, VD_ERR_CAPACITY);
+  return 0;
+}
+
+// Wait until queue slot h holds a pair, or the flood is over.  Lane 0 waits;
+// all lanes get the key (EMPTY_KEY: stop).  The wait is bounded by wall time.
+template <typename T>
+__device__ unsigned long long wait_item(const Dev<T>& C, long long h, int lane) {
+  unsigned long long key = EMPTY_KEY;
+  if (lane == 0) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    volatile unsigned long long* q = C.queue;
+    volatile unsigned long long* ctr = C.ctr;
+    volatile int* st = C.status;
+    for (;;) {
+      if (h < C.qcap) {
+        key = q[h];
+        if (key != EMPTY_KEY) break;
+      }
+      unsigned long long done = ctr[CTR_DONE];
+      __threadfence();
+      unsigned long long tail = ctr[CTR_TAIL];
+      if (done >= tail || *st != 0) { key = EMPTY_KEY; break; }
+      unsigned long long t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      if ((long long)(t1 - t0) > C.wait_ns) { set_error(C.status, VD_ERR_LIMIT); key = EMPTY_KEY; break; }
+      __nanosleep(128);
+    }
+  }
+  return __shfl_sync(FULL, key, 0);
+}
+
+template <typename T>
+__device__ __forceinline__ void stat_add(const Dev<T>& C, int slot, unsigned long long v) {
+  if (v) atomicAdd(C.stats + slot, v);
+}
+
+// ---------------------------------------------------------------------------
+// Point-in-cell test of a polytope corner (Sec. 3.1).
+//
+// q (frame of v_i) is a corner with coordinate error bound e; excl[] holds the
+// sites whose bisectors pass through it (its positive flags F_q).  The corner is
+// outside Omega_i iff some site k, not i and not in F_q, is strictly closer to
+// q than v_i (Eq. 1 with the flag rule of Sec. 3.1).  The grid is scanned ring
+// by ring around q; each candidate's difference of squared distances
+// f_k = |q - v_k|^2 - |q - v_i|^2 is compared with a bound B on its rounding
+// error (from e and the unit roundoff).  f_k < -B certifies "outside" and ends
+// the scan; |f_k| <= B is settled on the spot by the exact predicate `exact(k)`
+// (float64 on the defining planes) in the lane that met the site.  Without a
+// certified closer site the scan must cover the ball of radius |q - v_i| (plus
+// the error margin).  Returns 1 if outside; *wit gets the closer site with the
+// smallest (f_k, k) among the certified ones.
+// ---------------------------------------------------------------------------
+struct CornerScratch {
+  int pad;
+};
+
+template <typename T, typename Exact>
+__device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx, T qy, T qz, T e,
+                              const int* excl, int lane, ScanScratch& S, CornerScratch&, Exact& exact,
+                              int* wit, int* scanned) {
+  const T U = Prec<T>::U;
+  T gx = vix + qx, gy = viy + qy, gz = viz + qz;
+  T di2;
+  {
+    T dx = vix - gx, dy = viy - gy, dz = viz - gz;
+    di2 = dx * dx + dy * dy + dz * dz;
+  }
+  T di = sqrt(di2);
+  T gmax = fmax(fabs(gx), fmax(fabs(gy), fabs(gz)));
+  T delta = T(1.7320508075688772) * (e + T(2) * U * gmax);
+  T D = T(1.2) * di + delta;
+  T B = T(4.5) * D * delta + T(2.5) * delta * delta + T(16) * U * D * D;
+  bool well = delta <= T(0.03) * di;
+  T R = di * (T(1) + T(1e-5)) + T(2) * delta + T(4) * U * gmax;
+  // ill-conditioned corner: every site that could be closer goes to the exact test
+  T amb = well ? B : (R * R - di2) + B;
+  if (!well && lane == 0) atomicAdd(C.stats + VD_STAT_ILLCOND, 1ull);
+  int e0 = excl[0], e1 = excl[1], e2 = excl[2];
+  T bf = T(1e30), of = T(1e30);
+  int bk = 0x7fffffff, ok = 0x7fffffff;
+  auto visit = [&](const typename Prec<T>::V4& s) {
+    int k = site_id(s);
+    if (k == i || k == e0 || k == e1 || k == e2) return;
+    T dx = s.x - gx, dy = s.y - gy, dz = s.z - gz;
+    T f = (dx * dx + dy * dy + dz * dz) - di2;
+    if (f < bf || (f == bf && k < bk)) { bf = f; bk = k; }
+    if (f >= -B && f <= amb && (f < of || (f == of && k < ok)) && exact(k) < 0) { of = f; ok = k; }
+  };
+  int cx, cy, cz;
+  C.G.cell_of(gx, gy, gz, cx, cy, cz);
+  int r = 1;
+  *scanned += warp_scan_ring(C.G, cx, cy, cz, r, lane, S, visit);
+  for (;;) {
+    warp_argmin(bf, bk);
+    if (bf < -B) break;  // a certified closer site: outside, the ball need not be covered
+    T m = C.G.cover(cx, cy, cz, r, gx, gy, gz);
+    if (m >= T(1e29) || m >= R || r >= C.G.max_ring()) break;
+    ++r;
+    *scanned += warp_scan_ring(C.G, cx, cy, cz, r, lane, S, visit);
+  }
+  if (bf < -B) { *wit = bk; return 1; }
+  warp_argmin(of, ok);
+  if (ok != 0x7fffffff) { *wit = ok; return 1; }
+  *wit = -1;
+  return 0;
+}
+
+}  // namespace vd

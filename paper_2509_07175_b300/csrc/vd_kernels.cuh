@@ -1,0 +1,332 @@
+// vd_kernels.cuh -- the kernels of one diagram computation, in launch order:
+//   grid build (counting sort, Sec. 5.2), nearest-neighbour distances (Sec. 5.1),
+//   pair seeding (Alg. 4 / Alg. 5), the persistent clip-and-flood kernel (Alg. 3
+//   per pair, pairs discovered through face flags), and the per-site reduction
+//   (measure, centroid, neighbour CSR), plus Lloyd's update (Sec. 6.4).
+#pragma once
+
+#include <type_traits>
+
+#include "vd_clip3.cuh"
+#include "vd_clippoly.cuh"
+
+namespace vd {
+
+// ---------------------------------------------------------------------------
+// exclusive scan (3 phases: block scan with block sums, scan of the sums, add)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 512, SCAN_IPT = 8, SCAN_TILE = SCAN_T * SCAN_IPT;
+
+template <typename In, typename Out>
+__global__ void __launch_bounds__(SCAN_T) k_scan_tile(const In* in, Out* out, Out* bsum, long long n) {
+  __shared__ Out wsum[SCAN_T / WARP];
+  long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+  Out v[SCAN_IPT];
+  Out s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    v[k] = (base + k < n) ? (Out)in[base + k] : (Out)0;
+    s += v[k];
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  Out inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Out t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    Out x = lane < SCAN_T / WARP ? wsum[lane] : (Out)0;
+    Out xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      Out t = __shfl_up_sync(FULL, xi, o);
+      if (lane >= o) xi += t;
+    }
+    if (lane < SCAN_T / WARP) wsum[lane] = xi - x;
+    if (lane == SCAN_T / WARP - 1 && bsum) bsum[blockIdx.x] = xi;
+  }
+  __syncthreads();
+  Out run = wsum[w] + inc - s;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+template <typename Out>
+__global__ void k_scan_add(Out* out, const Out* boff, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += boff[i / SCAN_TILE];
+}
+
+// ---------------------------------------------------------------------------
+// site grid (counting sort by cell, x fastest)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_cell_count(Dev<T> C, int* cellid, int* count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  int cx, cy, cz;
+  C.G.cell_of(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], cx, cy, cz);
+  int c = (cz * C.G.gy + cy) * C.G.gx + cx;
+  cellid[i] = c;
+  atomicAdd(count + c, 1);
+}
+
+template <typename T>
+__global__ void k_cell_scatter(Dev<T> C, const int* cellid, const int* cstart, int* cursor,
+                               typename Prec<T>::V4* gs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  int c = cellid[i];
+  int pos = cstart[c] + atomicAdd(cursor + c, 1);
+  gs[pos] = Prec<T>::mk4(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], pack_id(T(0), i));
+}
+
+// delta_i = half the distance from v_i to its nearest other site (Sec. 5.1)
+template <typename T>
+__global__ void k_delta(Dev<T> C, T* delta) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  T d2;
+  int k = thread_nearest(C.G, C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], i, d2);
+  delta[i] = (k >= 0 && k < C.n) ? T(0.5) * sqrt(d2) : T(1);
+}
+
+// ---------------------------------------------------------------------------
+// seeding: (T_a, nearest site of T_a's centroid) for every simplex (Alg. 4), and
+// (simplex containing v_i, i) for every site inside the mesh
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_seed_simplex(Dev<T> C) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= C.m) return;
+  T c[3] = {0, 0, 0};
+  for (int l = 0; l < C.k; ++l)
+    for (int d = 0; d < 3; ++d) c[d] += C.verts[3 * C.simp[C.k * a + l] + d];
+  for (int d = 0; d < 3; ++d) c[d] /= T(C.k);
+  T d2;
+  int i = thread_nearest(C.G, c[0], c[1], c[2], -1, d2);
+  if (i >= 0 && i < C.n) push_pair(C, a, i);
+}
+
+struct Locator {
+  const int* start;   // [B+1]
+  const int* items;   // simplex ids
+  int bx, by, bz;
+  double ox, oy, oz, ih;
+};
+
+__device__ __forceinline__ double orient3(const double* a, const double* b, const double* c, const double* p) {
+  double ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
+  double vx = c[0] - a[0], vy = c[1] - a[1], vz = c[2] - a[2];
+  double wx = p[0] - a[0], wy = p[1] - a[1], wz = p[2] - a[2];
+  return ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx);
+}
+__device__ __forceinline__ double orient2(const double* a, const double* b, const double* p) {
+  return (b[0] - a[0]) * (p[1] - a[1]) - (b[1] - a[1]) * (p[0] - a[0]);
+}
+
+template <typename T>
+__global__ void k_seed_site(Dev<T> C, Locator L) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  double p[3] = {(double)C.sites[3 * i], (double)C.sites[3 * i + 1], (double)C.sites[3 * i + 2]};
+  int bx = (int)floor((p[0] - L.ox) * L.ih), by = (int)floor((p[1] - L.oy) * L.ih), bz = (int)floor((p[2] - L.oz) * L.ih);
+  if (bx < 0 || by < 0 || bz < 0 || bx >= L.bx || by >= L.by || bz >= L.bz) return;
+  int b = (bz * L.by + by) * L.bx + bx;
+  for (int t = L.start[b]; t < L.start[b + 1]; ++t) {
+    int a = L.items[t];
+    double V[4][3];
+    for (int l = 0; l < C.k; ++l)
+      for (int d = 0; d < 3; ++d) V[l][d] = (double)C.verts[3 * C.simp[C.k * a + l] + d];
+    bool in;
+    // barycentric signs: p substituted for each vertex keeps the orientation
+    if (C.k == 4) {
+      double o = orient3(V[0], V[1], V[2], V[3]);
+      double s0 = orient3(p, V[1], V[2], V[3]), s1 = orient3(V[0], p, V[2], V[3]);
+      double s2 = orient3(V[0], V[1], p, V[3]), s3 = orient3(V[0], V[1], V[2], p);
+      if (o < 0) { s0 = -s0; s1 = -s1; s2 = -s2; s3 = -s3; }
+      in = s0 >= 0 && s1 >= 0 && s2 >= 0 && s3 >= 0;
+    } else {
+      double o = orient2(V[0], V[1], V[2]);
+      double s0 = orient2(p, V[1], V[2]), s1 = orient2(V[0], p, V[2]), s2 = orient2(V[0], V[1], p);
+      if (o < 0) { s0 = -s0; s1 = -s1; s2 = -s2; }
+      in = s0 >= 0 && s1 >= 0 && s2 >= 0;
+    }
+    if (in) { push_pair(C, a, i); return; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent clip-and-flood: one warp per (simplex, site) pair, pairs taken
+// from the queue in order, new pairs appended by the flag rules
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+struct WarpOf {
+  using type = cp::WarpP<T>;
+};
+template <>
+struct WarpOf<float, VD_MODE_3D> {
+  using type = c3::Warp3;
+};
+
+constexpr int FLOOD_WARPS = 4;
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(FLOOD_WARPS * 32) k_flood(Dev<T> C) {
+  using W = typename WarpOf<T, MODE>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W& w = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
+  int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long h = 0;
+    if (lane == 0) h = atomicAdd(C.ctr + CTR_HEAD, 1ull);
+    h = __shfl_sync(FULL, h, 0);
+    unsigned long long key = wait_item(C, (long long)h, lane);
+    if (key == EMPTY_KEY) break;
+    int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
+    if constexpr (MODE == VD_MODE_3D) c3::process_pair(C, w, a, i, (long long)h, lane);
+    else cp::process_pair<T>(C, w, a, i, (long long)h, lane);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(C.ctr + CTR_DONE, 1ull);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-site reduction, deterministic: the pieces of a site are summed in order
+// of their simplex index whatever order the flood produced them in
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ long long npairs(const Dev<T>& C) {
+  unsigned long long t = C.ctr[CTR_TAIL];
+  return (long long)(t < (unsigned long long)C.qcap ? t : (unsigned long long)C.qcap);
+}
+
+template <typename T>
+__global__ void k_site_count(Dev<T> C, int* scnt) {
+  long long np = npairs(C);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
+    if (C.pmeas[p] > T(0)) atomicAdd(scnt + (int)(C.queue[p] & 0xffffffffull), 1);
+}
+
+template <typename T>
+__global__ void k_site_fill(Dev<T> C, const int* soff, int* scur, int* slist) {
+  long long np = npairs(C);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
+    if (C.pmeas[p] > T(0)) {
+      int i = (int)(C.queue[p] & 0xffffffffull);
+      slist[soff[i] + atomicAdd(scur + i, 1)] = (int)p;
+    }
+}
+
+template <typename T>
+__global__ void k_site_reduce(Dev<T> C, const int* soff, int* slist, T* measure, T* centroid, int* fc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  int b = soff[i], e = soff[i + 1];
+  for (int u = b + 1; u < e; ++u) {  // insertion sort by simplex index
+    int pu = slist[u];
+    unsigned au = (unsigned)(C.queue[pu] >> 32);
+    int v = u - 1;
+    while (v >= b && (unsigned)(C.queue[slist[v]] >> 32) > au) { slist[v + 1] = slist[v]; --v; }
+    slist[v + 1] = pu;
+  }
+  T m = 0, mx = 0, my = 0, mz = 0;
+  int nf = 0;
+  for (int u = b; u < e; ++u) {
+    int p = slist[u];
+    m += C.pmeas[p];
+    mx += C.pm1[3 * p];
+    my += C.pm1[3 * p + 1];
+    mz += C.pm1[3 * p + 2];
+    nf += C.pfcnt[p];
+  }
+  measure[i] = m;
+  T cx = C.sites[3 * i], cy = C.sites[3 * i + 1], cz = C.sites[3 * i + 2];
+  if (m > T(0)) { cx += mx / m; cy += my / m; cz += mz / m; }
+  centroid[3 * i] = cx;
+  centroid[3 * i + 1] = cy;
+  centroid[3 * i + 2] = cz;
+  fc[i] = nf;
+}
+
+template <typename T>
+__global__ void k_site_nbr(Dev<T> C, const int* soff, const int* slist, const int* foff, int* tmp, int* ucnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  int base = foff[i], c = 0;
+  for (int u = soff[i]; u < soff[i + 1]; ++u) {
+    int p = slist[u];
+    long long fo = C.pfoff[p];
+    for (int f = 0; f < C.pfcnt[p]; ++f) {
+      int x = C.pflags[fo + f];
+      if (x < 0) continue;
+      int v = c - 1;  // insertion into the sorted prefix, skipping duplicates
+      bool dup = false;
+      while (v >= 0 && tmp[base + v] >= x) {
+        if (tmp[base + v] == x) { dup = true; break; }
+        --v;
+      }
+      if (dup) continue;
+      for (int w = c; w > v + 1; --w) tmp[base + w] = tmp[base + w - 1];
+      tmp[base + v + 1] = x;
+      ++c;
+    }
+  }
+  ucnt[i] = c;
+}
+
+__global__ void k_site_nbr_copy(int n, const int* foff, const int* tmp, const long long* noff, int* nidx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long o = noff[i];
+  int c = (int)(noff[i + 1] - o);
+  for (int k = 0; k < c; ++k) nidx[o + k] = tmp[foff[i] + k];
+}
+
+template <typename T>
+__global__ void k_lloyd(int n, T* sites, const T* measure, const T* centroid) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !(measure[i] > T(0))) return;
+  sites[3 * i] = centroid[3 * i];
+  sites[3 * i + 1] = centroid[3 * i + 1];
+  sites[3 * i + 2] = centroid[3 * i + 2];
+}
+
+// piece export: simplex / site of every processed pair and its flags as a CSR
+template <typename T>
+__global__ void k_export_ids(Dev<T> C, int* ps, int* pi) {
+  long long np = npairs(C);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+    unsigned long long key = C.queue[p];
+    ps[p] = (int)(key >> 32);
+    pi[p] = (int)(key & 0xffffffffull);
+  }
+}
+
+template <typename T>
+__global__ void k_export_flags(Dev<T> C, const long long* xoff, int* xflags) {
+  long long np = npairs(C);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
+    for (int f = 0; f < C.pfcnt[p]; ++f) xflags[xoff[p] + f] = C.pflags[C.pfoff[p] + f];
+}
+
+// input conversion: n x dim (dim 2 or 3) of type S into n x 3 of type T
+template <typename S, typename T>
+__global__ void k_widen(const S* in, T* out, long long n, int dim) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[3 * i] = (T)in[dim * i];
+  out[3 * i + 1] = (T)in[dim * i + 1];
+  out[3 * i + 2] = dim == 3 ? (T)in[dim * i + 2] : T(0);
+}
+
+}  // namespace vd

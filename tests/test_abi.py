@@ -1,0 +1,47 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/vd.h (no compute call: no GPU needed)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vd_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2509_07175_b300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_header():
+    from paper_2509_07175_b300 import binding
+    assert sorted(binding.exported_symbols()) == _declared()
+
+
+def test_strerror_without_gpu():
+    from paper_2509_07175_b300 import binding, build
+    build.build()
+    lib = binding.load()
+    assert lib.vd_strerror(-4) == b"capacity exceeded (polytope, queue, pair set or flag buffer)"
+    assert lib.vd_strerror(0) == b"ok"
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu():
+    from paper_2509_07175_b300 import binding, build
+    build.build()
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    assert lib.vd_create(ctypes.byref(h), None, 10, 3, 0) == -1
+    assert lib.vd_create(ctypes.byref(h), ctypes.c_void_p(16), 0, 3, 0) == -1
+    assert lib.vd_create(ctypes.byref(h), ctypes.c_void_p(16), 10, 4, 0) == -1
+    assert lib.vd_create(ctypes.byref(h), ctypes.c_void_p(16), 10, 3, 7) == -1

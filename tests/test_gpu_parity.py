@@ -1,0 +1,128 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar (the benchmark spec): bit-exact neighbour sets and clip topology (the set of
+non-empty (simplex, site) pieces and each piece's face flags); per-site
+measures within 1e-5 relative; centroids within 1e-5 |c|.  Inputs are the
+seeded generators of ``paper_2509_07175_b300.inputs``.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2509_07175_b300 import inputs as I
+from vdcheck import compare_full, gpu_csr, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _w(mode, sites, verts, simp, f64=False, name="case"):
+    return dict(name=name, mode=mode, sites=sites, verts=verts, simp=simp, f64=f64)
+
+
+def _full_check(w, brute=False, options=None):
+    d, r, p = gpu_run(w, options=options)
+    assert r["status"] == 0
+    assert r["stats"]["uncertain"] == 0
+    op = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], brute=brute).enumerate()
+    assert op.stats["uncertain"] == 0
+    err = compare_full(w, r, p, op)
+    # pieces partition each simplex
+    per = np.zeros(len(w["simp"]))
+    pm = p["measure"].double().cpu().numpy()
+    np.add.at(per, p["simplex"].cpu().numpy(), pm)
+    # FP32 pieces: error ~ u x (cell size) relative to each piece, so the check is
+    # absolute, scaled by the mean cell measure |M| / n
+    ref = I.simplex_measures(w["mode"], w["verts"], w["simp"])
+    tol = 1e-5 * ref + 1e-5 * ref.sum() / len(w["sites"])
+    assert (np.abs(per - ref) <= tol).all(), np.abs(per - ref).max()
+    d.close()
+    return err
+
+
+def test_square_1000_fp64(gpu):
+    """Config 1 at full size: unit square as 2 triangles, 1,000 uniform sites, FP64."""
+    w = I.workload("square")
+    err = _full_check(w)
+    assert err["max_meas_rel"] < 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(1, 5), (2, 6), (37, 7), (500, 8)])
+def test_square_small_fp64(gpu, n, seed):
+    v, s = I.square_grid_tris(3)
+    w = _w(2, I.uniform_sites(n, 2, seed, f32=False), v, s, f64=True)
+    _full_check(w)
+
+
+def test_square_fp32(gpu):
+    v, s = I.square_grid_tris(4)
+    w = _w(2, I.uniform_sites(2000, 2, 9), v, s, f64=False)
+    _full_check(w)
+
+
+@pytest.mark.parametrize("dim,N", [(2, 8), (3, 4)])
+def test_lattice_closed_form(gpu, dim, N):
+    """Sites at box centres: cells are the boxes; exact ties resolve as inside."""
+    sites = I.lattice_sites(N, dim)
+    if dim == 2:
+        v, s = I.square_2tri()
+        w = _w(2, sites, v, s, f64=True)
+    else:
+        v, s = I.cube_6tet()
+        w = _w(4, sites, v, s, f64=False)
+    d, r, p = gpu_run(w)
+    assert r["status"] == 0
+    m = r["measure"].double().cpu().numpy()
+    c = r["centroid"].double().cpu().numpy()
+    assert np.abs(m - N ** -dim).max() <= 1e-6 * N ** -dim
+    assert np.abs(c - sites).max() <= 1e-6
+    nb = gpu_csr(r)
+    idx = np.round(sites[:, :dim] * N - 0.5).astype(int)
+    for i in range(len(sites)):
+        exp = sorted(int(j) for j in np.nonzero(np.abs(idx - idx[i]).sum(axis=1) == 1)[0])
+        assert nb[i] == exp
+
+
+@pytest.mark.parametrize("n,seed,grid", [(1, 21, 1), (2, 22, 1), (300, 23, 1), (3000, 24, 2)])
+def test_cube_small(gpu, n, seed, grid):
+    v, s = I.kuhn_lattice_tets(grid)
+    w = _w(4, I.uniform_sites(n, 3, seed), v, s)
+    _full_check(w)
+
+
+def test_shell_small_clustered(gpu):
+    v, s = I.small_shell(8)
+    w = _w(4, I.shell_sites(3000, seed=31, ncomp=4), v, s)
+    _full_check(w)
+
+
+def test_torus_small_surface(gpu):
+    v, s = I.small_torus(60, 20)
+    w = _w(3, I.surface_sites(1500, v, s, 41), v, s)
+    _full_check(w)
+
+
+def test_deterministic_bitwise(gpu):
+    v, s = I.kuhn_lattice_tets(2)
+    w = _w(4, I.uniform_sites(5000, 3, 51), v, s)
+    d, r1, p1 = gpu_run(w)
+    r2 = d.compute()
+    for k in ("measure", "centroid", "nbr_off", "nbr_idx"):
+        assert torch.equal(r1[k], r2[k]), k
+
+
+def test_cube_100k_sampled(gpu):
+    """Config 2 at full size: 100,000 sites in the 6-tet cube; oracle on a sample
+    of sites (all their pieces), plus the partition of the domain."""
+    w = I.workload("cube")
+    d, r, p = gpu_run(w)
+    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
+    pm = p["measure"].double().cpu().numpy()
+    assert abs(pm.sum() - 1.0) < 1e-5
+    per = np.zeros(6)
+    np.add.at(per, p["simplex"].cpu().numpy(), pm)
+    np.testing.assert_allclose(per, 1.0 / 6.0, rtol=1e-5)
+    rng = np.random.default_rng(7)
+    pick = np.sort(rng.choice(len(w["sites"]), 300, replace=False))
+    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
+    compare_full(w, r, p, op, sites_subset=pick)
