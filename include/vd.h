@@ -180,6 +180,36 @@ int vd_get_pieces(vd_ctx* ctx, vd_pieces* out);
  * output does not change.  k = 0 clears them. */
 int vd_set_candidates(vd_ctx* ctx, const int32_t* cand, int k);
 
+/* Piece export into caller-owned device buffers, with no device allocation.
+ *
+ * The paper has no counterpart: this is a service entry point.  vd_get_pieces
+ * allocates its export buffers on first use and its prefix sum uses scratch
+ * allocated with the context.  Some callers must not call cudaMalloc at the
+ * point where they read the pieces: a host framework whose caching allocator
+ * or fixed arena owns all device memory, or a steady-state loop where a
+ * cudaMalloc / cudaFree would synchronise the device.  This variant writes
+ * into buffers the caller already owns and keeps the prefix-sum scratch in a
+ * fixed array inside the library: 40,960 int64 (320 KiB) per device that
+ * loads the library, held until the process exits.
+ *
+ * simplex, site: int32 [pieces_capacity]; flag_off: int64 [pieces_capacity+1];
+ * flags: int32 [flags_capacity]; measure (context dtype [pieces_capacity]) and
+ * moment ([3*pieces_capacity]) may be NULL.  The number of pieces is
+ * vd_result.stats[VD_STAT_PAIRS] of the last vd_compute; *n_pieces and
+ * *n_flags receive the sizes written.  Layout and meaning as in vd_pieces.
+ * Returns VD_ERR_CAPACITY when the pieces exceed pieces_capacity or the limit
+ * of 67,108,863, or the flags exceed flags_capacity (nothing is written past a
+ * capacity); VD_ERR_STATE before the first vd_compute.  The first call on a
+ * device looks up the scratch array's device address (once per device); make
+ * that first call before any stream capture.  Every call on a device shares
+ * the same scratch array, which keeps the previous call's contents (the prefix
+ * sum overwrites all of it before reading), so calls that overlap on the GPU
+ * race: run them on one stream or one after another.  Synchronises the
+ * context stream. */
+int vd_get_pieces_noalloc(vd_ctx* ctx, int32_t* simplex, int32_t* site, int64_t* flag_off, int32_t* flags,
+                          void* measure, void* moment, int64_t pieces_capacity, int64_t flags_capacity,
+                          int64_t* n_pieces, int64_t* n_flags);
+
 /* Release everything owned by the context (NULL is allowed). */
 void vd_destroy(vd_ctx* ctx);
 

@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
         "vd_get_sites": ([P, P], I),
         "vd_get_pieces": ([P, ctypes.POINTER(PiecesC)], I),
         "vd_set_candidates": ([P, P, I], I),
+        "vd_get_pieces_noalloc": ([P, P, P, P, P, P, P, I64, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -90,7 +91,7 @@ def load(path: str = LIB_PATH):
 def exported_symbols():
     return ["vd_create", "vd_set_domain", "vd_set_options", "vd_set_stream", "vd_update_sites",
             "vd_update_sites_host", "vd_compute", "vd_copy_result_host", "vd_lloyd", "vd_get_sites",
-            "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror"]
+            "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc"]
 
 
 class _DevArray:

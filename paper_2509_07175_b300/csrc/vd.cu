@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -765,6 +766,78 @@ int vd_set_candidates(vd_ctx* c, const int32_t* cand, int k) {
   CK(cudaMemcpyAsync(p, cand, (size_t)c->n * k * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  return VD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Piece export without device allocation (vd_get_pieces_noalloc).
+//
+// The prefix sum over the per-piece flag counts needs block sums; here they live
+// in a fixed file-scope device array instead of context scratch.  Host code may
+// not use the array's name as a device address: the address is looked up once
+// per device with cudaGetSymbolAddress, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr long long NOALLOC_MAX_PIECES = (1ll << 26) - 1;
+constexpr size_t NOALLOC_SCRATCH = 40960;  // int64: block sums of a scan over <= 2^26 entries
+static __device__ __align__(256) long long g_noalloc_scratch[NOALLOC_SCRATCH];
+std::mutex g_noalloc_mu;
+long long* g_noalloc_addr[1024] = {};
+
+int noalloc_scratch(int device, long long** out) {
+  if (device < 0 || device >= 1024) return VD_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    int prev = 0;
+    CK(cudaGetDevice(&prev));
+    if (prev != device) CK(cudaSetDevice(device));
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess || !p) return VD_ERR_CUDA;
+    g_noalloc_addr[device] = static_cast<long long*>(p);
+  }
+  *out = g_noalloc_addr[device];
+  return VD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int vd_get_pieces_noalloc(vd_ctx* c, int32_t* simplex, int32_t* site, int64_t* flag_off, int32_t* flags,
+                          void* measure, void* moment, int64_t pieces_capacity, int64_t flags_capacity,
+                          int64_t* n_pieces, int64_t* n_flags) {
+  if (!c || !simplex || !site || !flag_off || !n_pieces || !n_flags || pieces_capacity < 0 || flags_capacity < 0)
+    return VD_ERR_ARG;
+  if (!c->computed) return VD_ERR_STATE;
+  static_assert(NOALLOC_MAX_PIECES + 1 <= (1ll << 26), "scan size");
+  if (scan_tmp_elems(NOALLOC_MAX_PIECES + 1) > NOALLOC_SCRATCH) return VD_ERR_CAPACITY;
+  long long np = c->last_pairs;
+  if (np > NOALLOC_MAX_PIECES || np > pieces_capacity) return VD_ERR_CAPACITY;
+  long long* scratch = nullptr;
+  int rc = noalloc_scratch(c->device, &scratch);
+  if (rc) return rc;
+  cudaStream_t s = c->stream;
+  long long* off = reinterpret_cast<long long*>(flag_off);
+  CK(cudaMemsetAsync(c->pfcnt + np, 0, sizeof(int), s));
+  if (c->dtype == VD_F64) k_export_ids<double><<<c->nsm * 8, 256, 0, s>>>(make_dev<double>(c), simplex, site);
+  else k_export_ids<float><<<c->nsm * 8, 256, 0, s>>>(make_dev<float>(c), simplex, site);
+  scan_excl<int, long long>(s, c->pfcnt, off, np + 1, scratch);
+  long long total = 0;
+  CK(cudaMemcpyAsync(&total, off + np, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (total > flags_capacity || (total > 0 && !flags)) return VD_ERR_CAPACITY;
+  if (c->dtype == VD_F64) k_export_flags<double><<<c->nsm * 8, 256, 0, s>>>(make_dev<double>(c), off, flags);
+  else k_export_flags<float><<<c->nsm * 8, 256, 0, s>>>(make_dev<float>(c), off, flags);
+  size_t ts = tsize(c->dtype);
+  if (measure && np) CK(cudaMemcpyAsync(measure, c->pmeas, (size_t)np * ts, cudaMemcpyDeviceToDevice, s));
+  if (moment && np) CK(cudaMemcpyAsync(moment, c->pm1, (size_t)np * 3 * ts, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  *n_pieces = np;
+  *n_flags = total;
   return VD_OK;
 }
 
