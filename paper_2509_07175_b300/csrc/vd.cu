@@ -50,6 +50,12 @@ struct vd_ctx {
   double ox = 0, oy = 0, oz = 0, h = 1;
   long long G = 0;
   int *cellid = nullptr, *ccount = nullptr, *cstart = nullptr, *ccur = nullptr;
+  int nlev = 1;                       // grid levels (level 0 dense, 1.. hashed)
+  float rho = 3.5f;                   // target sites per cell at the query level
+  int* lstart[MAX_LEVELS] = {};       // hashed levels: bucket starts
+  void* lgs[MAX_LEVELS] = {};         // hashed levels: sorted sites
+  long long lbuckets[MAX_LEVELS] = {};
+  unsigned char* qlev = nullptr;      // [G] query level of each level-0 cell
   void* gs = nullptr;
   void* delta = nullptr;
   unsigned long long *hash = nullptr, *queue = nullptr, *ctr = nullptr;
@@ -146,9 +152,18 @@ static Dev<T> make_dev(vd_ctx* c) {
   D.mode = c->mode; D.n = (int)c->n; D.m = (int)c->m; D.k = c->k;
   D.sites = (const T*)c->sites; D.verts = (const T*)c->verts; D.simp = c->simp; D.adj = c->adj; D.fsgn = c->fsgn;
   D.delta = (const T*)c->delta;
-  D.G.gs = (const typename Prec<T>::V4*)c->gs; D.G.cstart = c->cstart;
   D.G.gx = c->gx; D.G.gy = c->gy; D.G.gz = c->gz;
-  D.G.ox = (T)c->ox; D.G.oy = (T)c->oy; D.G.oz = (T)c->oz; D.G.h = (T)c->h; D.G.ih = (T)(1.0 / c->h);
+  D.G.ox = (T)c->ox; D.G.oy = (T)c->oy; D.G.oz = (T)c->oz;
+  D.G.nlev = c->nlev;
+  D.G.qlev = c->qlev;
+  for (int l = 0; l < c->nlev; ++l) {
+    double h = c->h / (double)(1 << l);
+    D.G.L[l].gs = (const typename Prec<T>::V4*)(l == 0 ? c->gs : c->lgs[l]);
+    D.G.L[l].start = l == 0 ? c->cstart : c->lstart[l];
+    D.G.L[l].mask = l == 0 ? 0u : (unsigned)(c->lbuckets[l] - 1);
+    D.G.L[l].h = (T)h;
+    D.G.L[l].ih = (T)(1.0 / h);
+  }
   D.cand = c->cand; D.ncand = c->ncand;
   D.hash = c->hash; D.hmask = c->hmask; D.queue = c->queue; D.qcap = c->qcap; D.ctr = c->ctr;
   D.pmeas = (T*)c->pmeas; D.pm1 = (T*)c->pm1; D.pfoff = c->pfoff; D.pfcnt = c->pfcnt; D.pflags = c->pflags;
@@ -202,13 +217,22 @@ static void enqueue_compute(vd_ctx* c) {
   cudaMemsetAsync(c->ctr, 0, sizeof(unsigned long long) * CTR_N, s);
   cudaMemsetAsync(c->hash, 0xFF, sizeof(unsigned long long) * (c->hmask + 1), s);
   cudaMemsetAsync(c->queue, 0xFF, sizeof(unsigned long long) * c->qcap, s);
-  cudaMemsetAsync(c->ccount, 0, sizeof(int) * (c->G + 1), s);
-  cudaMemsetAsync(c->ccur, 0, sizeof(int) * c->G, s);
   unsigned bn = nblk(c->n, 256);
-  k_cell_count<T><<<bn, 256, 0, s>>>(D, c->cellid, c->ccount);
-  scan_excl<int, int>(s, c->ccount, c->cstart, c->G + 1, (int*)c->scan_tmp);
-  k_cell_scatter<T><<<bn, 256, 0, s>>>(D, c->cellid, c->cstart, c->ccur, (typename Prec<T>::V4*)c->gs);
-  c->launches += 2 + scan_launches(c->G + 1);
+  for (int l = 0; l < c->nlev; ++l) {
+    long long nb = l == 0 ? c->G : c->lbuckets[l];
+    int* start = l == 0 ? c->cstart : c->lstart[l];
+    void* gs = l == 0 ? c->gs : c->lgs[l];
+    cudaMemsetAsync(c->ccount, 0, sizeof(int) * (nb + 1), s);
+    cudaMemsetAsync(c->ccur, 0, sizeof(int) * nb, s);
+    k_cell_count<T><<<bn, 256, 0, s>>>(D, l, c->cellid, c->ccount);
+    scan_excl<int, int>(s, c->ccount, start, nb + 1, (int*)c->scan_tmp);
+    k_cell_scatter<T><<<bn, 256, 0, s>>>(D, c->cellid, start, c->ccur, (typename Prec<T>::V4*)gs);
+    c->launches += 2 + scan_launches(nb + 1);
+    if (l == 0 && c->nlev > 1) {
+      k_query_level<<<nblk(c->G, 256), 256, 0, s>>>((int)c->G, c->cstart, c->qlev, c->nlev, c->rho);
+      c->launches += 1;
+    }
+  }
   mark(c, 1);
   k_delta<T><<<nblk(c->n, 128), 128, 0, s>>>(D, (T*)c->delta);
   mark(c, 2);
@@ -589,9 +613,31 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
       hh *= 1.25;
     }
     c->h = hh;
+    c->rho = (float)rho;
     c->ox = lo[0] - pad[0]; c->oy = lo[1] - pad[1]; c->oz = lo[2] - pad[2];
     if (mode == VD_MODE_2D) { c->oz = -0.5 * hh; }
     c->G = (long long)c->gx * c->gy * c->gz;
+    // levels for clustered sites: the densest level-0 cell of the current sites
+    // decides how many halvings of the cell edge are needed (3D and surface)
+    c->nlev = 1;
+    if (mode != VD_MODE_2D) {
+      std::vector<char> raw((size_t)c->n * 3 * ts);
+      CK(cudaMemcpy(raw.data(), c->sites, raw.size(), cudaMemcpyDeviceToHost));
+      std::vector<int> cnt((size_t)c->G, 0);
+      int mx = 0;
+      for (long long i = 0; i < c->n; ++i) {
+        double p[3];
+        for (int d = 0; d < 3; ++d)
+          p[d] = c->dtype == VD_F64 ? ((double*)raw.data())[3 * i + d] : (double)((float*)raw.data())[3 * i + d];
+        long long g[3] = {c->gx, c->gy, c->gz};
+        double o[3] = {c->ox, c->oy, c->oz};
+        long long ci[3];
+        for (int d = 0; d < 3; ++d) ci[d] = std::min<long long>(g[d] - 1, std::max<long long>(0, (long long)std::floor((p[d] - o[d]) / hh)));
+        int& k = cnt[(size_t)((ci[2] * c->gy + ci[1]) * c->gx + ci[0])];
+        mx = std::max(mx, ++k);
+      }
+      if (mx > 4 * rho) c->nlev = std::min(MAX_LEVELS, 1 + (int)std::ceil(std::log2((double)mx / rho) / 3.0));
+    }
   }
   // per-computation buffers
   long long n = c->n;
@@ -600,10 +646,22 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   while (hc < 2ull * (unsigned long long)c->qcap) hc <<= 1;
   c->hmask = hc - 1;
   c->fcap = 8 * c->qcap;
+  long long nbmax = c->G;
+  for (int l = 1; l < c->nlev; ++l) {
+    long long nb = 1;
+    while (nb < 2 * n) nb <<= 1;
+    c->lbuckets[l] = nb;
+    nbmax = std::max(nbmax, nb);
+    DALLOC(c->lstart[l], int, nb + 1, true);
+    char* p = nullptr;
+    rc = dalloc(c, p, (size_t)n * 4 * ts, true); if (rc) return rc;
+    c->lgs[l] = p;
+  }
+  DALLOC(c->qlev, unsigned char, c->G, true);
   DALLOC(c->cellid, int, n, true);
-  DALLOC(c->ccount, int, c->G + 1, true);
+  DALLOC(c->ccount, int, nbmax + 1, true);
   DALLOC(c->cstart, int, c->G + 1, true);
-  DALLOC(c->ccur, int, c->G + 1, true);
+  DALLOC(c->ccur, int, nbmax + 1, true);
   {
     char* p = nullptr;
     rc = dalloc(c, p, (size_t)n * 4 * ts, true); if (rc) return rc; c->gs = p;
@@ -630,7 +688,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   DALLOC(c->noff, long long, n + 1, true);
   DALLOC(c->nidx, int, c->fcap, true);
   {
-    long long L = std::max<long long>(c->G + 1, std::max<long long>(n + 1, c->qcap + 1));
+    long long L = std::max<long long>(nbmax + 1, std::max<long long>(n + 1, c->qcap + 1));
     long long* p = nullptr;
     rc = dalloc(c, p, scan_tmp_elems(L), true); if (rc) return rc;
     c->scan_tmp = p;

@@ -162,17 +162,22 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
     if (f < bf || (f == bf && k < bk)) { bf = f; bk = k; }
     if (f >= -B && f <= amb && (f < of || (f == of && k < ok)) && exact(k) < 0) { of = f; ok = k; }
   };
-  int cx, cy, cz;
-  C.G.cell_of(gx, gy, gz, cx, cy, cz);
-  int r = 1;
-  *scanned += warp_scan_ring(C.G, cx, cy, cz, r, lane, S, visit);
-  for (;;) {
-    warp_argmin(bf, bk);
-    if (bf < -B) break;  // a certified closer site: outside, the ball need not be covered
-    T m = C.G.cover(cx, cy, cz, r, gx, gy, gz);
-    if (m >= T(1e29) || m >= R || r >= C.G.max_ring()) break;
-    ++r;
-    *scanned += warp_scan_ring(C.G, cx, cy, cz, r, lane, S, visit);
+  for (int lev = C.G.query_level(gx, gy, gz); lev >= 0; --lev) {
+    int cx, cy, cz;
+    C.G.cell_at(lev, gx, gy, gz, cx, cy, cz);
+    int r = 1;
+    *scanned += warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S, visit);
+    bool done = false;
+    for (;;) {
+      warp_argmin(bf, bk);
+      if (bf < -B) { done = true; break; }  // a certified closer site: outside, no need to cover the ball
+      T m = C.G.cover(lev, cx, cy, cz, r, gx, gy, gz);
+      if (m >= T(1e29) || m >= R) { done = true; break; }
+      if (lev > 0 ? r >= HASH_MAX_RING : r >= C.G.max_ring()) break;
+      ++r;
+      *scanned += warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S, visit);
+    }
+    if (done) break;
   }
   if (bf < -B) { *wit = bk; return 1; }
   warp_argmin(of, ok);

@@ -64,15 +64,21 @@ __global__ void k_scan_add(Out* out, const Out* boff, long long n) {
 }
 
 // ---------------------------------------------------------------------------
-// site grid (counting sort by cell, x fastest)
+// site grids (counting sort by bucket: level-0 cell, x fastest, or hashed cell)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_cell_count(Dev<T> C, int* cellid, int* count) {
+__device__ __forceinline__ int bucket_of(const GridView<T>& G, int lev, T x, T y, T z) {
+  int cx, cy, cz;
+  G.cell_at(lev, x, y, z, cx, cy, cz);
+  if (lev == 0) return (cz * G.gy + cy) * G.gx + cx;
+  return (int)(cell_hash(cx, cy, cz) & G.L[lev].mask);
+}
+
+template <typename T>
+__global__ void k_cell_count(Dev<T> C, int lev, int* cellid, int* count) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C.n) return;
-  int cx, cy, cz;
-  C.G.cell_of(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], cx, cy, cz);
-  int c = (cz * C.G.gy + cy) * C.G.gx + cx;
+  int c = bucket_of(C.G, lev, C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   cellid[i] = c;
   atomicAdd(count + c, 1);
 }
@@ -85,6 +91,17 @@ __global__ void k_cell_scatter(Dev<T> C, const int* cellid, const int* cstart, i
   int c = cellid[i];
   int pos = cstart[c] + atomicAdd(cursor + c, 1);
   gs[pos] = Prec<T>::mk4(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], pack_id(T(0), i));
+}
+
+// query level of every level-0 cell: the level whose cells hold about rho sites
+// at the cell's own density (each level halves the cell edge)
+__global__ void k_query_level(int G0, const int* cstart0, unsigned char* qlev, int nlev, float rho) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G0) return;
+  float cnt = (float)(cstart0[c + 1] - cstart0[c]);
+  int l = 0;
+  if (cnt > rho) l = (int)floorf(log2f(cnt / rho) / 3.f + 0.5f);
+  qlev[c] = (unsigned char)min(l, nlev - 1);
 }
 
 // delta_i = half the distance from v_i to its nearest other site (Sec. 5.1)

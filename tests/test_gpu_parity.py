@@ -126,3 +126,18 @@ def test_cube_100k_sampled(gpu):
     pick = np.sort(rng.choice(len(w["sites"]), 300, replace=False))
     op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
     compare_full(w, r, p, op, sites_subset=pick)
+
+
+def test_shell_1m_sampled(gpu):
+    """Config 3 at full size: 1,000,000 clustered sites in the tetrahedralised shell
+    (172,032 tets); oracle on a sample of sites, plus the partition of the shell."""
+    w = I.workload("shell")
+    d, r, p = gpu_run(w)
+    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
+    pm = p["measure"].double().cpu().numpy()
+    total = I.domain_measure(4, w["verts"], w["simp"])
+    assert abs(pm.sum() - total) < 1e-5 * total
+    rng = np.random.default_rng(11)
+    pick = np.sort(rng.choice(len(w["sites"]), 200, replace=False))
+    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
+    compare_full(w, r, p, op, sites_subset=pick)
