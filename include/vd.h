@@ -95,6 +95,7 @@ typedef struct {
   int max_lambda;          /* start-point steps per clip (0: 64) */
   double wait_limit_s;     /* longest wait of an idle worker on the queue (0: 10 s) */
   int timing;              /* 1: time the phases of vd_compute with CUDA events */
+  double grid_density;     /* target sites per grid cell (0: 2.0); read by vd_set_domain */
 } vd_options;
 
 typedef struct {

@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
     _fields_ = [("learned", ctypes.c_int), ("mapping", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("stats", ctypes.c_int), ("queue_capacity", ctypes.c_int64), ("max_clips", ctypes.c_int),
                 ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("grid_density", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):

@@ -598,7 +598,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   {
     double pad[3];
     for (int d = 0; d < 3; ++d) pad[d] = 1e-3 * (hi[d] - lo[d]) + 1e-6;
-    double rho = mode == VD_MODE_3D ? 3.5 : 2.5;
+    double rho = c->opt.grid_density > 0 ? c->opt.grid_density : 2.0;
     double hh = mode == VD_MODE_3D ? std::cbrt(measure * rho / (double)c->n) : std::sqrt(measure * rho / (double)c->n);
     double e[3];
     for (int d = 0; d < 3; ++d) e[d] = hi[d] - lo[d] + 2 * pad[d];

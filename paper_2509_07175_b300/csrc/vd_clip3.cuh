@@ -95,7 +95,7 @@ __device__ __forceinline__ void plane_bis(const Dev<float>& C, int j, float3 vi,
 }
 
 // float64 plane from its source, with running error bounds
-__device__ ePlane eplane(const Dev<float>& C, int a, int i, int src) {
+__device__ __noinline__ ePlane eplane(const Dev<float>& C, int a, int i, int src) {
   ed3 vi{mk(C.sites[3 * i]), mk(C.sites[3 * i + 1]), mk(C.sites[3 * i + 2])};
   ePlane p;
   if (src >= 0) {
@@ -139,8 +139,14 @@ __device__ float4 corner(float4 P0, float2 M0, float4 P1, float2 M1, float4 P2, 
   return make_float4(qx, qy, qz, e);
 }
 
+// loose FP32 bound: recompute the corner from its exact planes in float64
+__device__ __noinline__ float4 refine64(const Dev<float>& C, int a, int i, int s0, int s1, int s2) {
+  atomicAdd(C.stats + VD_STAT_FP64, 1ull);
+  return corner64(eplane(C, a, i, s0), eplane(C, a, i, s1), eplane(C, a, i, s2));
+}
+
 // ----- exact side tests ----------------------------------------------------------
-__device__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4) {
+__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4) {
   ePlane p[4];
   uchar4 v = W.tv[t];
   // the corner lies on each of its own planes: the side value is exactly zero
@@ -186,8 +192,8 @@ __device__ __forceinline__ void add_plane(Warp3& W, int slot, float4 P, float2 M
 }
 
 // nearest site through the warp (counted)
-__device__ __forceinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, float y, float z, int lane,
-                                        Counters& K) {
+__device__ __noinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, float y, float z, int lane,
+                                     Counters& K) {
   float d2;
   int sc = 0;
   int k = warp_nearest(C.G, x, y, z, lane, W.S, d2, &sc);
@@ -198,7 +204,7 @@ __device__ __forceinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, 
 
 // Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
 // Returns the bisector site j for the outside corner t.
-__device__ int find_bisector(const Dev<float>& C, Warp3& W, int i, float3 vi, int t, int lane, Counters& K) {
+__device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, float3 vi, int t, int lane, Counters& K) {
   float4 q = W.tq[t];
   int wit = W.twit[t];
   float dist = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
@@ -233,7 +239,7 @@ __device__ int find_bisector(const Dev<float>& C, Warp3& W, int i, float3 vi, in
 
 // Clip by the plane in slot pl, removing the component of outside corners that
 // contains p.  Returns 0 (clipped), 1 (P became empty), -1 (error, status set).
-__device__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, int pl, int p, int lane) {
+__device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, int pl, int p, int lane) {
   unsigned om[3], R[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -262,76 +268,65 @@ __device__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, int 
     if (!ch) break;
   }
   if (R[0] == Mk.alive[0] && R[1] == Mk.alive[1] && R[2] == Mk.alive[2]) return 1;
-  // boundary edges of R: (x -> y) of a removed corner whose neighbour u is kept
-  int cnt[3];
-  int ex[3][3], ey[3][3], eu[3][3];
-#pragma unroll
+  // boundary edges of R: (x -> y) of a removed corner whose neighbour u is kept.
+  // Each lane lists its edges (at most 3 corners x 3 edges), packed x | y << 8 | u << 16.
+  int cnt = 0;
+  unsigned edge[9];
+#pragma unroll 1
   for (int r = 0; r < 3; ++r) {
     int t = r * 32 + lane;
-    cnt[r] = 0;
-    if (bit(R, t)) {
-      uchar4 v = W.tv[t], nb = W.tn[t];
-      int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
-#pragma unroll
-      for (int e = 0; e < 3; ++e)
-        if (!bit(R, nn[e])) { ex[r][cnt[r]] = vv[e]; ey[r][cnt[r]] = vv[(e + 1) % 3]; eu[r][cnt[r]] = nn[e]; cnt[r]++; }
-    }
+    if (!bit(R, t)) continue;
+    uchar4 v = W.tv[t], nb = W.tn[t];
+    int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
+#pragma unroll 1
+    for (int e = 0; e < 3; ++e)
+      if (!bit(R, nn[e])) edge[cnt++] = (unsigned)vv[e] | ((unsigned)vv[(e + 1) % 3] << 8) | ((unsigned)nn[e] << 16);
   }
   unsigned fr[3] = {~Mk.alive[0] | R[0], ~Mk.alive[1] | R[1], ~Mk.alive[2] | R[2]};
   int nfree = __popc(fr[0]) + __popc(fr[1]) + __popc(fr[2]);
-  int base[3], total = 0;
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    int inc = warp_incl_scan(cnt[r], lane);
-    base[r] = total + inc - cnt[r];
-    total += __shfl_sync(FULL, inc, 31);
-  }
+  int inc = warp_incl_scan(cnt, lane);
+  int base = inc - cnt;
+  int total = __shfl_sync(FULL, inc, 31);
   if (total > nfree || total < 3) { set_error(C.status, total < 3 ? VD_ERR_LIMIT : VD_ERR_CAPACITY); return -1; }
   // reset the loop maps, then claim them
   __syncwarp();
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < cnt[r]; ++c) { W.stri[ex[r][c]] = -1; W.etri[ey[r][c]] = -1; }
+#pragma unroll 1
+  for (int c = 0; c < cnt; ++c) { W.stri[edge[c] & 255u] = -1; W.etri[(edge[c] >> 8) & 255u] = -1; }
   __syncwarp();
-  int slot[3][3];
+  int c0 = __popc(fr[0]), c1 = __popc(fr[1]);
   bool bad = false;
   unsigned newm[3] = {0, 0, 0};
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < cnt[r]; ++c) {
-      int k = base[r] + c;
-      int c0 = __popc(fr[0]), c1 = __popc(fr[1]);
-      int s = k < c0 ? nth_set(fr[0], k) : (k < c0 + c1 ? 32 + nth_set(fr[1], k - c0) : 64 + nth_set(fr[2], k - c0 - c1));
-      slot[r][c] = s;
-      if (atomicExch(&W.stri[ex[r][c]], s) != -1) bad = true;
-      if (atomicExch(&W.etri[ey[r][c]], s) != -1) bad = true;
-    }
+  int slot[9];
+#pragma unroll 1
+  for (int c = 0; c < cnt; ++c) {
+    int k = base + c;
+    int sl = k < c0 ? nth_set(fr[0], k) : (k < c0 + c1 ? 32 + nth_set(fr[1], k - c0) : 64 + nth_set(fr[2], k - c0 - c1));
+    slot[c] = sl;
+    if (atomicExch(&W.stri[edge[c] & 255u], sl) != -1) bad = true;
+    if (atomicExch(&W.etri[(edge[c] >> 8) & 255u], sl) != -1) bad = true;
+  }
   if (__any_sync(FULL, bad)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
   __syncwarp();
   // write the new corners (their slots held removed corners or were free)
   float4 Pn = W.pn[pl];
   float2 Mn = W.pm[pl];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < cnt[r]; ++c) {
-      int s = slot[r][c], x = ex[r][c], y = ey[r][c], u = eu[r][c];
-      W.tv[s] = make_uchar4((unsigned char)x, (unsigned char)y, (unsigned char)pl, 0);
-      W.tn[s] = make_uchar4((unsigned char)u, (unsigned char)W.stri[y], (unsigned char)W.etri[x], 0);
-      uchar4 uv = W.tv[u];
-      if (uv.x == y && uv.y == x) W.tn[u].x = (unsigned char)s;
-      else if (uv.y == y && uv.z == x) W.tn[u].y = (unsigned char)s;
-      else if (uv.z == y && uv.x == x) W.tn[u].z = (unsigned char)s;
-      else bad = true;
-      float4 qc = corner(W.pn[x], W.pm[x], W.pn[y], W.pm[y], Pn, Mn);
-      if (!(qc.w <= 3e-3f * sqrtf(qc.x * qc.x + qc.y * qc.y + qc.z * qc.z))) {
-        // loose FP32 bound: recompute the corner from its exact planes in float64
-        qc = corner64(eplane(C, a, i, W.psrc[x]), eplane(C, a, i, W.psrc[y]), eplane(C, a, i, W.psrc[pl]));
-        atomicAdd(C.stats + VD_STAT_FP64, 1ull);
-      }
-      W.tq[s] = qc;
-      W.twit[s] = -1;
-      newm[s >> 5] |= 1u << (s & 31);
-    }
+#pragma unroll 1
+  for (int c = 0; c < cnt; ++c) {
+    int sl = slot[c], x = edge[c] & 255u, y = (edge[c] >> 8) & 255u, u = edge[c] >> 16;
+    W.tv[sl] = make_uchar4((unsigned char)x, (unsigned char)y, (unsigned char)pl, 0);
+    W.tn[sl] = make_uchar4((unsigned char)u, (unsigned char)W.stri[y], (unsigned char)W.etri[x], 0);
+    uchar4 uv = W.tv[u];
+    if (uv.x == y && uv.y == x) W.tn[u].x = (unsigned char)sl;
+    else if (uv.y == y && uv.z == x) W.tn[u].y = (unsigned char)sl;
+    else if (uv.z == y && uv.x == x) W.tn[u].z = (unsigned char)sl;
+    else bad = true;
+    float4 qc = corner(W.pn[x], W.pm[x], W.pn[y], W.pm[y], Pn, Mn);
+    if (!(qc.w <= 3e-3f * sqrtf(qc.x * qc.x + qc.y * qc.y + qc.z * qc.z)))
+      qc = refine64(C, a, i, W.psrc[x], W.psrc[y], W.psrc[pl]);
+    W.tq[sl] = qc;
+    W.twit[sl] = -1;
+    newm[sl >> 5] |= 1u << (sl & 31);
+  }
   __syncwarp();
   if (__any_sync(FULL, bad)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
 #pragma unroll
@@ -396,7 +391,7 @@ __device__ void check_mesh(const Dev<float>& C, Warp3& W, const Masks& Mk, int a
 
 // Integrate volume, first moment (frame of v_i) and face areas of the current
 // polytope; sigma is +-1 (orientation of the dual mesh against space).
-__device__ void integrate(Warp3& W, const Masks& Mk, float sigma, int lane, float& vol, float3& m1) {
+__device__ __noinline__ void integrate(Warp3& W, const Masks& Mk, float sigma, int lane, float& vol, float3& m1) {
   for (int x = lane; x < MAXP; x += 32) {
     W.pref[x] = 0x7fffffff;
     W.parea[x][0] = W.parea[x][1] = W.parea[x][2] = 0.f;
@@ -416,18 +411,18 @@ __device__ void integrate(Warp3& W, const Masks& Mk, float sigma, int lane, floa
   __syncwarp();
   float4 O = W.tq[o];
   float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
+#pragma unroll 1
   for (int r = 0; r < 3; ++r) {
     int t = r * 32 + lane;
     if (!bit(Mk.alive, t)) continue;
     uchar4 v = W.tv[t], nb = W.tn[t];
-    int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
     float4 A4 = W.tq[t];
     float ax = A4.x - O.x, ay = A4.y - O.y, az = A4.z - O.z;
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < 3; ++e) {
-      int x = vv[e];
-      float4 R4 = W.tq[W.pref[x]], B4 = W.tq[nn[e]];
+      int x = e == 0 ? v.x : (e == 1 ? v.y : v.z);
+      int ne = e == 0 ? nb.x : (e == 1 ? nb.y : nb.z);
+      float4 R4 = W.tq[W.pref[x]], B4 = W.tq[ne];
       float rx = R4.x - O.x, ry = R4.y - O.y, rz = R4.z - O.z;
       float bx = B4.x - O.x, by = B4.y - O.y, bz = B4.z - O.z;
       float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
@@ -480,8 +475,17 @@ __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i,
   __syncwarp();
 }
 
+#ifdef VD_PROFILE
+#define PROF_T0() long long _t0 = clock64()
+#define PROF_ADD(k) do { long long _t1 = clock64(); if (lane == 0) atomicAdd(C.stats + 24 + (k), (unsigned long long)(_t1 - _t0)); _t0 = _t1; } while (0)
+#else
+#define PROF_T0() do {} while (0)
+#define PROF_ADD(k) do {} while (0)
+#endif
+
 __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long long slot, int lane) {
   Counters K = {0, 0, 0, 0, 0, 0, 0, 0};
+  PROF_T0();
   float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   Masks Mk;
   init_tet(C, W, Mk, a, i, vi, lane);
@@ -494,6 +498,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   }
   bool empty = false;
   int nclip = 0;
+  PROF_ADD(0);
   for (;;) {
     // first corner (in slot order) outside Omega_i; each corner is tested once
     int p = -1;
@@ -524,9 +529,11 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       }
       Mk.in[t >> 5] |= 1u << (t & 31);
     }
+    PROF_ADD(1);
     if (p < 0) break;
     if (++nclip > C.max_clips) { set_error(C.status, VD_ERR_LIMIT); return; }
     int j = find_bisector(C, W, i, vi, p, lane, K);
+    PROF_ADD(2);
     // free plane slot for B_ij
     unsigned long long freep = ~Mk.palive & ((1ull << MAXP) - 1ull);
     if (!freep) { set_error(C.status, VD_ERR_CAPACITY); return; }
@@ -544,6 +551,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
     }
     int rc = clip(C, W, Mk, a, i, pl, p, lane);
     K.clips++;
+    PROF_ADD(3);
     if (rc < 0) return;
 #ifdef VD_CHECK
     if (rc == 0) check_mesh(C, W, Mk, a, i, pl, lane);
@@ -586,6 +594,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   unsigned lt = (1u << lane) - 1u;
   if (has[0]) C.pflags[fbase + __popc(b0 & lt)] = myflag[0];
   if (has[1]) C.pflags[fbase + __popc(b0) + __popc(b1 & lt)] = myflag[1];
+  PROF_ADD(4);
   if (lane == 0) {
     C.pmeas[slot] = nonempty ? vol : 0.f;
     C.pm1[3 * slot] = nonempty ? m1.x : 0.f;

@@ -91,7 +91,7 @@ __device__ void plane_B(const Dev<T>& C, int j, const T* vi, typename Prec<T>::V
 }
 
 template <typename T>
-__device__ ePlane eplane(const Dev<T>& C, int a, int i, int src) {
+__device__ __noinline__ ePlane eplane(const Dev<T>& C, int a, int i, int src) {
   ed3 vi{mk(C.sites[3 * i]), mk(C.sites[3 * i + 1]), mk(C.sites[3 * i + 2])};
   ePlane p;
   if (src >= 0) {
@@ -139,7 +139,7 @@ __device__ typename Prec<T>::V4 corner(const WarpP<T>& W, int p0, int p1, int p2
 
 // a corner whose FP32 error bound is loose is recomputed from its exact planes
 template <typename T>
-__device__ __forceinline__ typename Prec<T>::V4 refine(const Dev<T>& C, const WarpP<T>& W, int a, int i,
+__device__ __noinline__ typename Prec<T>::V4 refine(const Dev<T>& C, const WarpP<T>& W, int a, int i,
                                                        typename Prec<T>::V4 q, int p1, int p2) {
   if (sizeof(T) == 8) return q;
   if (q.w <= T(3e-3) * sqrt(q.x * q.x + q.y * q.y + q.z * q.z)) return q;
@@ -149,7 +149,7 @@ __device__ __forceinline__ typename Prec<T>::V4 refine(const Dev<T>& C, const Wa
 }
 
 template <typename T>
-__device__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4) {
+__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4) {
   int km = (k + nv - 1) % nv;
   // the corner lies on each of its own planes: the side value is exactly zero
   if (src4 == -1 || src4 == W.psrc[W.ve[km]] || src4 == W.psrc[W.ve[k]]) return 0;
@@ -186,7 +186,7 @@ struct Counters {
 };
 
 template <typename T>
-__device__ __forceinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z, int lane, Counters& K) {
+__device__ __noinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z, int lane, Counters& K) {
   T d2;
   int sc = 0;
   int k = warp_nearest(C.G, x, y, z, lane, W.S, d2, &sc);
@@ -196,7 +196,7 @@ __device__ __forceinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, 
 }
 
 template <typename T>
-__device__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, const T* vi, int k, int lane, Counters& K) {
+__device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, const T* vi, int k, int lane, Counters& K) {
   typename Prec<T>::V4 q = W.vq[k];
   int wit = W.vwit[k];
   T dist = sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
@@ -232,7 +232,7 @@ __device__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, const T* vi, i
 // clip the ring by plane pl, removing the outside run that contains corner p.
 // returns 0 clipped, 1 empty, -1 error.  nv is updated.
 template <typename T>
-__device__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int pl, int p, int& nv, int lane) {
+__device__ __noinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int pl, int p, int& nv, int lane) {
   bool o = lane < nv && side_of(C, W, a, i, lane, nv, pl) < 0;
   unsigned om = __ballot_sync(FULL, o);
   if (!((om >> p) & 1u)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
@@ -253,8 +253,14 @@ __device__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int pl, int p, i
     q = W.vq[src]; ve = W.ve[src]; st = W.vst[src]; wt = W.vwit[src];
   }
   typename Prec<T>::V4 X, Y;
-  if (lane == keep) X = refine(C, W, a, i, corner(W, 0, eX, pl), eX, pl);
-  if (lane == keep + 1) Y = refine(C, W, a, i, corner(W, 0, pl, eY), pl, eY);
+  if (lane == keep) {
+    X = corner(W, 0, eX, pl);
+    if (sizeof(T) == 4 && !(X.w <= T(3e-3) * sqrt(X.x * X.x + X.y * X.y + X.z * X.z))) X = refine(C, W, a, i, X, eX, pl);
+  }
+  if (lane == keep + 1) {
+    Y = corner(W, 0, pl, eY);
+    if (sizeof(T) == 4 && !(Y.w <= T(3e-3) * sqrt(Y.x * Y.x + Y.y * Y.y + Y.z * Y.z))) Y = refine(C, W, a, i, Y, pl, eY);
+  }
   __syncwarp();
   if (lane < keep) { W.vq[lane] = q; W.ve[lane] = ve; W.vst[lane] = st; W.vwit[lane] = wt; }
   if (lane == keep) { W.vq[lane] = X; W.ve[lane] = pl; W.vst[lane] = 0; W.vwit[lane] = -1; }

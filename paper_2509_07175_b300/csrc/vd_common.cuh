@@ -72,6 +72,14 @@ template <typename T> __device__ __forceinline__ void warp_argmin(T& d, int& id)
     if (od < d || (od == d && (unsigned)oi < (unsigned)id)) { d = od; id = oi; }
   }
 }
+// float values >= 0 (squared distances): two warp reductions on the bit patterns
+// (non-negative floats order like their bits) instead of a shuffle tree
+template <> __device__ __forceinline__ void warp_argmin<float>(float& d, int& id) {
+  unsigned m = __reduce_min_sync(FULL, __float_as_uint(d));
+  unsigned c = __float_as_uint(d) == m ? (unsigned)id : 0xffffffffu;
+  id = (int)__reduce_min_sync(FULL, c);
+  d = __uint_as_float(m);
+}
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll

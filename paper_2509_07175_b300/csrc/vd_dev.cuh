@@ -152,35 +152,34 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
   T amb = well ? B : (R * R - di2) + B;
   if (!well && lane == 0) atomicAdd(C.stats + VD_STAT_ILLCOND, 1ull);
   int e0 = excl[0], e1 = excl[1], e2 = excl[2];
-  T bf = T(1e30), of = T(1e30);
+  // minimum of the squared distance d_k^2 (>= 0) over the candidates; f = d_k^2 - d_i^2
+  T bd = T(1e30), od = T(1e30);
   int bk = 0x7fffffff, ok = 0x7fffffff;
   auto visit = [&](const typename Prec<T>::V4& s) {
     int k = site_id(s);
     if (k == i || k == e0 || k == e1 || k == e2) return;
     T dx = s.x - gx, dy = s.y - gy, dz = s.z - gz;
-    T f = (dx * dx + dy * dy + dz * dz) - di2;
-    if (f < bf || (f == bf && k < bk)) { bf = f; bk = k; }
-    if (f >= -B && f <= amb && (f < of || (f == of && k < ok)) && exact(k) < 0) { of = f; ok = k; }
+    T d2 = dx * dx + dy * dy + dz * dz;
+    T f = d2 - di2;
+    if (d2 < bd || (d2 == bd && k < bk)) { bd = d2; bk = k; }
+    if (f >= -B && f <= amb && (d2 < od || (d2 == od && k < ok)) && exact(k) < 0) { od = d2; ok = k; }
   };
   for (int lev = C.G.query_level(gx, gy, gz); lev >= 0; --lev) {
     int cx, cy, cz;
     C.G.cell_at(lev, gx, gy, gz, cx, cy, cz);
-    int r = 1;
-    *scanned += warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S, visit);
     bool done = false;
-    for (;;) {
-      warp_argmin(bf, bk);
-      if (bf < -B) { done = true; break; }  // a certified closer site: outside, no need to cover the ball
+    for (int r = 1;; ++r) {
+      *scanned += warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S, visit);
+      warp_argmin(bd, bk);
+      if (bd - di2 < -B) { done = true; break; }  // a certified closer site: outside, no need to cover the ball
       T m = C.G.cover(lev, cx, cy, cz, r, gx, gy, gz);
       if (m >= T(1e29) || m >= R) { done = true; break; }
       if (lev > 0 ? r >= HASH_MAX_RING : r >= C.G.max_ring()) break;
-      ++r;
-      *scanned += warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S, visit);
     }
     if (done) break;
   }
-  if (bf < -B) { *wit = bk; return 1; }
-  warp_argmin(of, ok);
+  if (bd - di2 < -B) { *wit = bk; return 1; }
+  warp_argmin(od, ok);
   if (ok != 0x7fffffff) { *wit = ok; return 1; }
   *wit = -1;
   return 0;

@@ -144,11 +144,41 @@ __device__ __forceinline__ void ring_segment(const GridView<T>& G, int lev, int 
   e = __ldg(G.L[0].start + base + x1 + 1);
 }
 
-// Warp-cooperative visit of every site of ring r on a level; visit(site4) runs
-// on the lane that owns the site.  Returns the number of sites visited.
+// Ring 1 (the 3x3x3 block), the common case, without a prefix sum: on level 0
+// three lanes share each of the 9 x-rows (sites strided by 3), on a hashed
+// level each of 27 lanes takes one cell.  Loads are independent across lanes.
 template <typename T, typename Visit>
-__device__ __forceinline__ int warp_scan_ring(const GridView<T>& G, int lev, int cx, int cy, int cz, int r,
-                                              int lane, ScanScratch& S, Visit& visit) {
+__device__ __forceinline__ int warp_scan_block(const GridView<T>& G, int lev, int cx, int cy, int cz, int lane,
+                                               Visit& visit) {
+  const typename Prec<T>::V4* gs = G.L[lev].gs;
+  int b = 0, e = 0, step = 1;
+  if (lane < 27) {
+    if (lev == 0) {
+      int row = lane / 3, j = lane - 3 * row;
+      int y = cy + row % 3 - 1, z = cz + row / 3 - 1;
+      if (y >= 0 && y < G.gy && z >= 0 && z < G.gz) {
+        int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < G.gx ? cx + 1 : G.gx - 1;
+        int base = (z * G.gy + y) * G.gx;
+        b = __ldg(G.L[0].start + base + x0) + j;
+        e = __ldg(G.L[0].start + base + x1 + 1);
+        step = 3;
+      }
+    } else {
+      int dx = lane % 3 - 1, t = lane / 3;
+      unsigned k = cell_hash(cx + dx, cy + t % 3 - 1, cz + t / 3 - 1) & G.L[lev].mask;
+      b = __ldg(G.L[lev].start + k);
+      e = __ldg(G.L[lev].start + k + 1);
+    }
+  }
+  int seen = e > b ? (e - b + step - 1) / step : 0;
+  for (int p = b; p < e; p += step) visit(gs[p]);
+  return __reduce_add_sync(FULL, (unsigned)seen);
+}
+
+// Rings r >= 2 (rare): segments prefix-summed across the lanes, flattened list.
+template <typename T, typename Visit>
+__device__ __noinline__ int warp_scan_shell(const GridView<T>& G, int lev, int cx, int cy, int cz, int r,
+                                            int lane, ScanScratch& S, Visit& visit) {
   int nslots = ring_slots(lev, r);
   const typename Prec<T>::V4* gs = G.L[lev].gs;
   int seen = 0;
@@ -180,6 +210,15 @@ __device__ __forceinline__ int warp_scan_ring(const GridView<T>& G, int lev, int
   return seen;
 }
 
+// Warp-cooperative visit of every site of ring r on a level; visit(site4) runs
+// on the lane that owns the site.  Returns the number of sites visited.
+template <typename T, typename Visit>
+__device__ __forceinline__ int warp_scan_ring(const GridView<T>& G, int lev, int cx, int cy, int cz, int r,
+                                              int lane, ScanScratch& S, Visit& visit) {
+  if (r == 1) return warp_scan_block(G, lev, cx, cy, cz, lane, visit);
+  return warp_scan_shell(G, lev, cx, cy, cz, r, lane, S, visit);
+}
+
 // Nearest site of q (ties: smaller index), warp-cooperative ring search.
 // Returns the index; d2 receives the squared distance.  All lanes get the result.
 template <typename T>
@@ -197,16 +236,13 @@ __device__ int warp_nearest(const GridView<T>& G, T qx, T qy, T qz, int lane, Sc
   for (int lev = G.query_level(qx, qy, qz); lev >= 0; --lev) {
     int cx, cy, cz;
     G.cell_at(lev, qx, qy, qz, cx, cy, cz);
-    int r = 1;
-    seen += warp_scan_ring(G, lev, cx, cy, cz, r, lane, S, visit);
     bool done = false;
-    for (;;) {
+    for (int r = 1;; ++r) {
+      seen += warp_scan_ring(G, lev, cx, cy, cz, r, lane, S, visit);
       warp_argmin(bd, bi);
       T m = G.cover(lev, cx, cy, cz, r, qx, qy, qz);
       if (m >= T(1e29) || (m > 0 && bd <= m * m)) { done = true; break; }
       if (lev > 0 ? r >= HASH_MAX_RING : r >= G.max_ring()) break;
-      ++r;
-      seen += warp_scan_ring(G, lev, cx, cy, cz, r, lane, S, visit);
     }
     if (done || lev == 0) break;
   }
@@ -243,15 +279,12 @@ __device__ int thread_nearest(const GridView<T>& G, T qx, T qy, T qz, int skip, 
   for (int lev = G.query_level(qx, qy, qz); lev >= 0; --lev) {
     int cx, cy, cz;
     G.cell_at(lev, qx, qy, qz, cx, cy, cz);
-    int r = 1;
-    thread_scan_ring(G, lev, cx, cy, cz, r, visit);
     bool done = false;
-    for (;;) {
+    for (int r = 1;; ++r) {
+      thread_scan_ring(G, lev, cx, cy, cz, r, visit);
       T m = G.cover(lev, cx, cy, cz, r, qx, qy, qz);
       if (m >= T(1e29) || (m > 0 && bd <= m * m)) { done = true; break; }
       if (lev > 0 ? r >= HASH_MAX_RING : r >= G.max_ring()) break;
-      ++r;
-      thread_scan_ring(G, lev, cx, cy, cz, r, visit);
     }
     if (done || lev == 0) break;
   }

@@ -100,7 +100,7 @@ __global__ void k_query_level(int G0, const int* cstart0, unsigned char* qlev, i
   if (c >= G0) return;
   float cnt = (float)(cstart0[c + 1] - cstart0[c]);
   int l = 0;
-  if (cnt > rho) l = (int)floorf(log2f(cnt / rho) / 3.f + 0.5f);
+  if (cnt > rho) l = (int)ceilf(log2f(cnt / rho) / 3.f - 0.15f);
   qlev[c] = (unsigned char)min(l, nlev - 1);
 }
 
@@ -193,9 +193,12 @@ struct WarpOf<float, VD_MODE_3D> {
 };
 
 constexpr int FLOOD_WARPS = 4;
+#ifndef FLOOD_MIN_BLOCKS
+#define FLOOD_MIN_BLOCKS 4
+#endif
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(FLOOD_WARPS * 32) k_flood(Dev<T> C) {
+__global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(Dev<T> C) {
   using W = typename WarpOf<T, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W& w = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
@@ -204,7 +207,13 @@ __global__ void __launch_bounds__(FLOOD_WARPS * 32) k_flood(Dev<T> C) {
     unsigned long long h = 0;
     if (lane == 0) h = atomicAdd(C.ctr + CTR_HEAD, 1ull);
     h = __shfl_sync(FULL, h, 0);
+#ifdef VD_PROFILE
+    long long tw = clock64();
+#endif
     unsigned long long key = wait_item(C, (long long)h, lane);
+#ifdef VD_PROFILE
+    if (lane == 0) atomicAdd(C.stats + 29, (unsigned long long)(clock64() - tw));
+#endif
     if (key == EMPTY_KEY) break;
     int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
     if constexpr (MODE == VD_MODE_3D) c3::process_pair(C, w, a, i, (long long)h, lane);
