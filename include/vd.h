@@ -77,6 +77,8 @@ enum {
   VD_STAT_ERROR_LINE = 15,    /* source line of the first device-side error (diagnostics) */
   VD_STAT_DIAG = 16,          /* 16..23: first FP64 decision that was not certified or was an
                                  exact tie: simplex, site, the 4 plane sources, tie flag, kind */
+  VD_STAT_LIST_TESTS = 30,    /* point-in-cell tests and queries settled from the 32 nearest
+                                 sites of the cell's site, with no grid scan (learned form) */
   VD_STAT_N = 32
 };
 
@@ -95,7 +97,8 @@ typedef struct {
   int max_lambda;          /* start-point steps per clip (0: 64) */
   double wait_limit_s;     /* longest wait of an idle worker on the queue (0: 10 s) */
   int timing;              /* 1: time the phases of vd_compute with CUDA events */
-  double grid_density;     /* target sites per grid cell (0: 2.0); read by vd_set_domain */
+  double grid_density;     /* target sites per grid cell (0: 3.0); read by vd_set_domain */
+  int topk;                /* candidates per site used by the learned proposal (0: 16, max 32) */
 } vd_options;
 
 typedef struct {

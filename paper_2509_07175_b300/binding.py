@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
     _fields_ = [("learned", ctypes.c_int), ("mapping", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("stats", ctypes.c_int), ("queue_capacity", ctypes.c_int64), ("max_clips", ctypes.c_int),
                 ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
-                ("timing", ctypes.c_int), ("grid_density", ctypes.c_double)]
+                ("timing", ctypes.c_int), ("grid_density", ctypes.c_double), ("topk", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -184,7 +184,8 @@ class Diagram:
             "nbr_idx": _view(r.nbr_idx, (int(r.nnz),), torch.int32).clone(),
             "n_pieces": int(r.n_pieces),
             "stats": dict(zip(STAT_NAMES, [int(x) for x in r.stats][:len(STAT_NAMES)]),
-                          error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]]),
+                          error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]],
+                          list_tests=int(r.stats[30])),
             "phase_ms": dict(zip(PHASE_NAMES, [float(x) for x in r.phase_ms][:len(PHASE_NAMES)])),
         }
         return out

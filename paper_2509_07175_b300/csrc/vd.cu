@@ -73,8 +73,11 @@ struct vd_ctx {
   void* scan_tmp = nullptr;
   int *xs = nullptr, *xi = nullptr, *xflags = nullptr;
   long long* xoff = nullptr;
-  int* cand = nullptr;
+  int* cand = nullptr;            // candidates set by the caller (vd_set_candidates)
   int ncand = 0;
+  int* knn = nullptr;             // [n*32] nearest sites (learned proposal)
+  float* knn_d2 = nullptr;
+  int* lcand = nullptr;           // [n*32] candidates computed by the library
   int flood_grid = 0;
   size_t flood_smem = 0;
   bool have_domain = false;
@@ -110,6 +113,8 @@ static void resolve_options(vd_options& o) {
   if (o.max_clips <= 0) o.max_clips = 256;
   if (o.max_search <= 0) o.max_search = 256;
   if (o.max_lambda <= 0) o.max_lambda = 64;
+  if (o.topk <= 0) o.topk = 16;
+  if (o.topk > 32) o.topk = 32;
   if (!(o.wait_limit_s > 0)) o.wait_limit_s = 10.0;
 }
 
@@ -164,7 +169,11 @@ static Dev<T> make_dev(vd_ctx* c) {
     D.G.L[l].h = (T)h;
     D.G.L[l].ih = (T)(1.0 / h);
   }
-  D.cand = c->cand; D.ncand = c->ncand;
+  if (c->cand) { D.cand = c->cand; D.ncand = c->ncand; }
+  else if (c->opt.learned && c->lcand) { D.cand = c->lcand; D.ncand = c->opt.topk; }
+  else { D.cand = nullptr; D.ncand = 0; }
+  D.knn = (c->opt.learned && !c->cand) ? c->knn : nullptr;
+  D.knn_d2 = c->knn_d2;
   D.hash = c->hash; D.hmask = c->hmask; D.queue = c->queue; D.qcap = c->qcap; D.ctr = c->ctr;
   D.pmeas = (T*)c->pmeas; D.pm1 = (T*)c->pm1; D.pfoff = c->pfoff; D.pfcnt = c->pfcnt; D.pflags = c->pflags;
   D.fcap = c->fcap;
@@ -235,10 +244,17 @@ static void enqueue_compute(vd_ctx* c) {
   }
   mark(c, 1);
   k_delta<T><<<nblk(c->n, 128), 128, 0, s>>>(D, (T*)c->delta);
+  c->launches += 1;
+  if (c->opt.learned && !c->cand) {
+    // learned proposal: the 32 nearest sites, ranked into the candidate list
+    k_knn<T><<<c->nsm * 8, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
+    k_cand_from_knn<<<nblk(c->n * (long long)c->opt.topk, 256), 256, 0, s>>>((int)c->n, c->opt.topk, c->knn, c->lcand);
+    c->launches += 2;
+  }
   mark(c, 2);
   k_seed_simplex<T><<<nblk(c->m, 128), 128, 0, s>>>(D);
   if (MODE != VD_MODE_SURFACE) k_seed_site<T><<<nblk(c->n, 128), 128, 0, s>>>(D, c->L);
-  c->launches += MODE != VD_MODE_SURFACE ? 3 : 2;
+  c->launches += MODE != VD_MODE_SURFACE ? 2 : 1;
   mark(c, 3);
   k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D);
   c->launches += 1;
@@ -598,7 +614,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   {
     double pad[3];
     for (int d = 0; d < 3; ++d) pad[d] = 1e-3 * (hi[d] - lo[d]) + 1e-6;
-    double rho = c->opt.grid_density > 0 ? c->opt.grid_density : 2.0;
+    double rho = c->opt.grid_density > 0 ? c->opt.grid_density : 3.0;
     double hh = mode == VD_MODE_3D ? std::cbrt(measure * rho / (double)c->n) : std::sqrt(measure * rho / (double)c->n);
     double e[3];
     for (int d = 0; d < 3; ++d) e[d] = hi[d] - lo[d] + 2 * pad[d];
@@ -658,6 +674,9 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
     c->lgs[l] = p;
   }
   DALLOC(c->qlev, unsigned char, c->G, true);
+  DALLOC(c->knn, int, n * KNN, true);
+  DALLOC(c->knn_d2, float, n * KNN, true);
+  DALLOC(c->lcand, int, n * KNN, true);
   DALLOC(c->cellid, int, n, true);
   DALLOC(c->ccount, int, nbmax + 1, true);
   DALLOC(c->cstart, int, c->G + 1, true);

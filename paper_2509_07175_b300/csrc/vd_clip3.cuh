@@ -37,6 +37,8 @@ struct Warp3 {
   int stri[MAXP], etri[MAXP];  // boundary loop: new corner starting / ending at a plane
   int pref[MAXP];       // reference corner of each face (integration)
   float parea[MAXP][3]; // face vector areas
+  unsigned long long pkey[MAXP];  // smallest corner key of each face (integration)
+  float4 contrib[MAXT]; // volume / moment terms by corner rank (integration)
   ScanScratch S;
   CornerScratch A;
 };
@@ -202,6 +204,36 @@ __device__ __noinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, flo
   return k;
 }
 
+// nearest site of the search point v_i + s.  Learned form: when 2|s| <= r32 the
+// nearest site is v_i or one of v_i's 32 nearest sites (any site at least as close
+// to the point as v_i lies within 2|s| of v_i), found with no grid scan.
+__device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, int i, float3 vi, float sx, float sy,
+                                         float sz, int lane, Counters& K) {
+  float px = vi.x + sx, py = vi.y + sy, pz = vi.z + sz;
+  if (C.knn && C.knn[(long long)i * 32 + 31] >= 0 && C.knn_d2[(long long)i * 32 + 31] > 0.f) {
+    float r32 = sqrtf(C.knn_d2[(long long)i * 32 + 31] * (1.f - 1e-6f));
+    float s = sqrtf(sx * sx + sy * sy + sz * sz);
+    if (2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= r32) {
+      int k = C.knn[(long long)i * 32 + lane];
+      float d2 = 1e30f;
+      int kk = 0x7fffffff;
+      if (k >= 0) {
+        float dx = C.sites[3 * k] - px, dy = C.sites[3 * k + 1] - py, dz = C.sites[3 * k + 2] - pz;
+        d2 = dx * dx + dy * dy + dz * dz;
+        kk = k;
+      }
+      float dxi = vi.x - px, dyi = vi.y - py, dzi = vi.z - pz;
+      float di2 = dxi * dxi + dyi * dyi + dzi * dzi;
+      if (lane == 0 && (di2 < d2 || (di2 == d2 && i < kk))) { d2 = di2; kk = i; }
+      warp_argmin(d2, kk);
+      if (lane == 0) atomicAdd(C.stats + VD_STAT_LIST_TESTS, 1ull);
+      K.nn++;
+      return kk;
+    }
+  }
+  return nn_query(C, W, px, py, pz, lane, K);
+}
+
 // Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
 // Returns the bisector site j for the outside corner t.
 __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, float3 vi, int t, int lane, Counters& K) {
@@ -212,6 +244,32 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, 
   float gx = q.x, gy = q.y, gz = q.z;
   int j = wit;
   float delta = C.delta[i];
+  if (C.ncand > 0) {
+    // learned proposal, shortcut: the first crossing of the ray v_i -> p with a
+    // candidate bisector (or the witness's); one query there either confirms it as
+    // the exit point of Omega_i or restarts the plain search from it (Sec. 3.2)
+    float tb = 1.f;
+    int cb = 0x7fffffff;
+    int k = lane < C.ncand ? C.cand[(long long)i * C.ncand + lane] : (lane == 31 ? wit : -1);
+    if (k >= 0 && k != i) {
+      float wx = C.sites[3 * k] - vi.x, wy = C.sites[3 * k + 1] - vi.y, wz = C.sites[3 * k + 2] - vi.z;
+      float den = wx * q.x + wy * q.y + wz * q.z;
+      if (den > 0.f) {
+        float tt = 0.5f * (wx * wx + wy * wy + wz * wz) / den;
+        if (tt < tb) { tb = tt; cb = k; }
+      }
+    }
+    warp_argmin(tb, cb);
+    if (cb != 0x7fffffff) {
+      float sx = q.x * tb, sy = q.y * tb, sz = q.z * tb;
+      int kk = nn_search(C, W, i, vi, sx, sy, sz, lane, K);
+      K.search++;
+      if (kk == i || kk == cb) { K.learned++; return cb; }
+      j = kk;
+      gx = sx; gy = sy; gz = sz;
+      goto search;
+    }
+  }
   for (int lam = 2; lam < 2 + C.max_lambda; ++lam) {
     float step = (float)lam * delta;
     if (!(step < dist)) break;
@@ -220,6 +278,7 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, 
     K.lam++;
     if (k != i) { gx = sx; gy = sy; gz = sz; j = k; break; }
   }
+search:
   for (int s = 0; s < C.max_search; ++s) {
     float wx = C.sites[3 * j] - vi.x, wy = C.sites[3 * j + 1] - vi.y, wz = C.sites[3 * j + 2] - vi.z;
     float den = wx * gx + wy * gy + wz * gz;
@@ -227,7 +286,7 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, 
     float tt = 0.5f * (wx * wx + wy * wy + wz * wz) / den;
     if (!(tt < 1.f)) return j;   // the bisector meets the segment at its end
     float sx = gx * tt, sy = gy * tt, sz = gz * tt;
-    int k = nn_query(C, W, vi.x + sx, vi.y + sy, vi.z + sz, lane, K);
+    int k = nn_search(C, W, i, vi, sx, sy, sz, lane, K);
     K.search++;
     if (k == i || k == j) return j;
     j = k;
@@ -389,40 +448,109 @@ __device__ void check_mesh(const Dev<float>& C, Warp3& W, const Masks& Mk, int a
 }
 #endif
 
-// Integrate volume, first moment (frame of v_i) and face areas of the current
-// polytope; sigma is +-1 (orientation of the dual mesh against space).
-__device__ __noinline__ void integrate(Warp3& W, const Masks& Mk, float sigma, int lane, float& vol, float3& m1) {
+// Canonical key of a corner: its three plane sources (bisector site j -> j+4,
+// tet face f -> f), sorted, 21 bits each.  Equal for the same corner whatever
+// sequence of clips produced it (sites beyond 2^21-5 fall back to slot order).
+__device__ __forceinline__ unsigned long long corner_key(int s0, int s1, int s2) {
+  unsigned a = (unsigned)(s0 + 4), b = (unsigned)(s1 + 4), c = (unsigned)(s2 + 4);
+  unsigned t;
+  if (a > b) { t = a; a = b; b = t; }
+  if (b > c) { t = b; b = c; c = t; }
+  if (a > b) { t = a; a = b; b = t; }
+  return ((unsigned long long)(a & 0x1fffffu) << 42) | ((unsigned long long)(b & 0x1fffffu) << 21) |
+         (unsigned long long)(c & 0x1fffffu);
+}
+
+// Integrate volume, first moment (frame of v_i) and face areas of the final
+// polytope, independently of the clip history: every corner is recomputed from
+// its three planes taken in key order (tet vertices directly from the mesh), the
+// reference corner of each face and the origin are the smallest-key corners, and
+// the terms are summed in corner-key order.  sigma is +-1 (orientation of the
+// dual mesh against space).
+__device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Masks& Mk, int a, int i, float3 vi,
+                                       float sigma, int lane, float& vol, float3& m1) {
   for (int x = lane; x < MAXP; x += 32) {
     W.pref[x] = 0x7fffffff;
+    W.pkey[x] = ~0ull;
     W.parea[x][0] = W.parea[x][1] = W.parea[x][2] = 0.f;
   }
   __syncwarp();
+  unsigned long long key[3];
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    int t = r * 32 + lane;
+    key[r] = ~0ull;
+    if (!bit(Mk.alive, t)) continue;
+    uchar4 v = W.tv[t];
+    int pl[3] = {v.x, v.y, v.z};
+    int sr[3] = {W.psrc[v.x], W.psrc[v.y], W.psrc[v.z]};
+    // planes in key order
+    for (int u = 0; u < 2; ++u)
+      for (int w = 0; w < 2 - u; ++w)
+        if (sr[w] + 4 > sr[w + 1] + 4) { int tt = sr[w]; sr[w] = sr[w + 1]; sr[w + 1] = tt; tt = pl[w]; pl[w] = pl[w + 1]; pl[w + 1] = tt; }
+    float4 q;
+    if (sr[2] < 0) {
+      int k = 6 - (-1 - sr[0]) - (-1 - sr[1]) - (-1 - sr[2]);  // tet vertex off the three faces
+      const float* V = C.verts + 3 * C.simp[4 * a + k];
+      float qx = V[0] - vi.x, qy = V[1] - vi.y, qz = V[2] - vi.z;
+      q = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
+    } else {
+      q = corner(W.pn[pl[0]], W.pm[pl[0]], W.pn[pl[1]], W.pm[pl[1]], W.pn[pl[2]], W.pm[pl[2]]);
+      if (!(q.w <= 3e-3f * sqrtf(q.x * q.x + q.y * q.y + q.z * q.z))) q = refine64(C, a, i, sr[0], sr[1], sr[2]);
+    }
+    W.tq[t] = q;
+    key[r] = corner_key(sr[0], sr[1], sr[2]);
+    atomicMin(&W.pkey[v.x], key[r]); atomicMin(&W.pkey[v.y], key[r]); atomicMin(&W.pkey[v.z], key[r]);
+  }
+  __syncwarp();
+  // rank of each corner among all corners (keys are distinct for distinct corners)
+  int rank[3] = {0, 0, 0};
+#pragma unroll 1
+  for (int j = 0; j < 32; ++j) {
+    unsigned long long k0 = __shfl_sync(FULL, key[0], j), k1 = __shfl_sync(FULL, key[1], j),
+                       k2 = __shfl_sync(FULL, key[2], j);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      int tr = r * 32 + lane;
+      rank[r] += (k0 < key[r] || (k0 == key[r] && j < tr)) + (k1 < key[r] || (k1 == key[r] && 32 + j < tr)) +
+                 (k2 < key[r] || (k2 == key[r] && 64 + j < tr));
+    }
+  }
   int o = -1;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     int t = r * 32 + lane;
-    if (bit(Mk.alive, t)) {
-      uchar4 v = W.tv[t];
-      atomicMin(&W.pref[v.x], t); atomicMin(&W.pref[v.y], t); atomicMin(&W.pref[v.z], t);
-    }
-    unsigned m = Mk.alive[r];
-    if (o < 0 && m) o = r * 32 + __ffs(m) - 1;
+    if (key[r] == ~0ull) continue;
+    uchar4 v = W.tv[t];
+    if (W.pkey[v.x] == key[r]) W.pref[v.x] = t;
+    if (W.pkey[v.y] == key[r]) W.pref[v.y] = t;
+    if (W.pkey[v.z] == key[r]) W.pref[v.z] = t;
+    if (rank[r] == 0) o = t;
   }
+  o = __reduce_max_sync(FULL, (unsigned)(o + 1)) - 1;
   __syncwarp();
   float4 O = W.tq[o];
-  float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+  int nalive = __popc(Mk.alive[0]) + __popc(Mk.alive[1]) + __popc(Mk.alive[2]);
 #pragma unroll 1
   for (int r = 0; r < 3; ++r) {
     int t = r * 32 + lane;
-    if (!bit(Mk.alive, t)) continue;
+    if (key[r] == ~0ull) continue;
     uchar4 v = W.tv[t], nb = W.tn[t];
     float4 A4 = W.tq[t];
     float ax = A4.x - O.x, ay = A4.y - O.y, az = A4.z - O.z;
+    // the corner's three edge terms, faces in key order
+    int fx[3] = {v.x, v.y, v.z}, fn[3] = {nb.x, nb.y, nb.z};
+    int sr[3] = {W.psrc[v.x] + 4, W.psrc[v.y] + 4, W.psrc[v.z] + 4};
+    int ord[3] = {0, 1, 2};
+    for (int u = 0; u < 2; ++u)
+      for (int w = 0; w < 2 - u; ++w)
+        if (sr[ord[w]] > sr[ord[w + 1]]) { int tt = ord[w]; ord[w] = ord[w + 1]; ord[w + 1] = tt; }
+    float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll 1
-    for (int e = 0; e < 3; ++e) {
-      int x = e == 0 ? v.x : (e == 1 ? v.y : v.z);
-      int ne = e == 0 ? nb.x : (e == 1 ? nb.y : nb.z);
-      float4 R4 = W.tq[W.pref[x]], B4 = W.tq[ne];
+    for (int e3 = 0; e3 < 3; ++e3) {
+      int e = ord[e3];
+      int x = fx[e];
+      float4 R4 = W.tq[W.pref[x]], B4 = W.tq[fn[e]];
       float rx = R4.x - O.x, ry = R4.y - O.y, rz = R4.z - O.z;
       float bx = B4.x - O.x, by = B4.y - O.y, bz = B4.z - O.z;
       float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
@@ -435,6 +563,17 @@ __device__ __noinline__ void integrate(Warp3& W, const Masks& Mk, float sigma, i
       atomicAdd(&W.parea[x][0], uy * wz - uz * wy);
       atomicAdd(&W.parea[x][1], uz * wx - ux * wz);
       atomicAdd(&W.parea[x][2], ux * wy - uy * wx);
+    }
+    W.contrib[rank[r]] = make_float4(v6, mx, my, mz);
+  }
+  __syncwarp();
+  float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    int k = r * 32 + lane;
+    if (k < nalive) {
+      float4 c4 = W.contrib[k];
+      v6 += c4.x; mx += c4.y; my += c4.z; mz += c4.w;
     }
   }
   v6 = warp_sum(v6);
@@ -489,12 +628,18 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   Masks Mk;
   init_tet(C, W, Mk, a, i, vi, lane);
+  // orientation of the dual mesh against space: with the corner table below, the
+  // edge-term sum of integrate() has the sign of the tet's orientation
   float sigma;
   {
-    float v0;
-    float3 m0;
-    integrate(W, Mk, 1.f, lane, v0, m0);
-    sigma = v0 < 0.f ? -1.f : 1.f;
+    const int* sp = C.simp + 4 * a;
+    const float *P0 = C.verts + 3 * sp[0], *P1 = C.verts + 3 * sp[1], *P2 = C.verts + 3 * sp[2],
+                *P3 = C.verts + 3 * sp[3];
+    double ux = (double)P1[0] - P0[0], uy = (double)P1[1] - P0[1], uz = (double)P1[2] - P0[2];
+    double vx = (double)P2[0] - P0[0], vy = (double)P2[1] - P0[1], vz = (double)P2[2] - P0[2];
+    double wx = (double)P3[0] - P0[0], wy = (double)P3[1] - P0[1], wz = (double)P3[2] - P0[2];
+    double det = ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx);
+    sigma = det > 0 ? 1.f : -1.f;
   }
   bool empty = false;
   int nclip = 0;
@@ -560,7 +705,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   }
   float vol = 0.f;
   float3 m1 = make_float3(0.f, 0.f, 0.f);
-  if (!empty) integrate(W, Mk, sigma, lane, vol, m1);
+  if (!empty) integrate(C, W, Mk, a, i, vi, sigma, lane, vol, m1);
   bool nonempty = !empty && vol > 0.f;
   // faces of positive area: output flags and propagate (Alg. 4 / Alg. 5 rules)
   int nflag = 0;
@@ -610,6 +755,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       stat_add(C, VD_STAT_SEARCH_STEPS, K.search);
       stat_add(C, VD_STAT_SITES_SCANNED, K.scanned);
       stat_add(C, VD_STAT_FALLBACK, K.fallback);
+      stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
     }
   }
   __syncwarp();

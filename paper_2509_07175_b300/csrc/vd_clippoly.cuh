@@ -344,16 +344,44 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
     if (rc < 0) return;
     if (rc == 1) { empty = true; break; }
   }
-  // integrate: area and first moment by a fan from corner 0 in the plane S
+  // integrate: area and first moment by a fan in the plane S, independently of
+  // the clip history: corners recomputed from their planes in source order
+  // (triangle vertices directly from the mesh), the fan starts at the corner with
+  // the smallest key (sorted sources of its two edge planes) and runs in ring order
   T area = 0, mx = 0, my = 0, mz = 0;
   bool nonempty = false;
   if (!empty) {
+    unsigned khi = 0xffffffffu, klo = 0xffffffffu;
+    if (lane < nv) {
+      int km = (lane + nv - 1) % nv;
+      int pa = W.ve[km], pb = W.ve[lane];
+      int sa = W.psrc[pa], sb = W.psrc[pb];
+      V4 q;
+      if (sa < -1 && sb < -1) {
+        const T* V = vtx(C, a, -2 - sb);  // edge e starts at local vertex e
+        T qx = V[0] - vi[0], qy = V[1] - vi[1], qz = V[2] - vi[2];
+        q = Prec<T>::mk4(qx, qy, qz, T(2) * Prec<T>::U * fmax(fabs(qx), fmax(fabs(qy), fabs(qz))));
+      } else {
+        if (sa + 8 > sb + 8) { int t = pa; pa = pb; pb = t; }
+        q = corner(W, 0, pa, pb);
+        if (sizeof(T) == 4 && !(q.w <= T(3e-3) * sqrt(q.x * q.x + q.y * q.y + q.z * q.z))) q = refine(C, W, a, i, q, pa, pb);
+      }
+      unsigned ua = (unsigned)(sa + 8), ub = (unsigned)(sb + 8);
+      khi = min(ua, ub);
+      klo = max(ua, ub);
+      __syncwarp(__activemask());
+      W.vq[lane] = q;
+    }
+    __syncwarp();
+    unsigned mh = __reduce_min_sync(FULL, khi);
+    unsigned ml = __reduce_min_sync(FULL, khi == mh ? klo : 0xffffffffu);
+    int st = (int)__reduce_min_sync(FULL, (khi == mh && klo == ml) ? (unsigned)lane : 0xffffffffu);
     V4 S = W.pn[0];
     T sl = sqrt(S.x * S.x + S.y * S.y + S.z * S.z);
     T nx = S.x / sl, ny = S.y / sl, nz = S.z / sl;
-    V4 O = W.vq[0];
+    V4 O = W.vq[st];
     if (lane >= 1 && lane + 1 < nv) {
-      V4 A = W.vq[lane], B = W.vq[lane + 1];
+      V4 A = W.vq[(st + lane) % nv], B = W.vq[(st + lane + 1) % nv];
       T ax = A.x - O.x, ay = A.y - O.y, az = A.z - O.z;
       T bx = B.x - O.x, by = B.y - O.y, bz = B.z - O.z;
       T cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;

@@ -20,9 +20,11 @@ struct Dev {
   const signed char* fsgn;  // [m*k] +-1: orientation making the face normal point outward
   const T* delta;        // [n] half the distance to the nearest other site (Sec. 5.1)
   GridView<T> G;
-  // learned proposal
+  // learned proposal: candidate bisector neighbours of each site (ranked)
   const int* cand;       // [n*ncand] candidate neighbours, -1 unused
-  int ncand;
+  int ncand;             // 0: plain search (Sec. 3.2 / 5.1 only)
+  const int* knn;        // [n*32] nearest other sites, ascending (learned form), or null
+  const float* knn_d2;   // [n*32] their squared distances (FP32)
   // pair set and queue
   unsigned long long* hash;
   unsigned long long hmask;
@@ -164,6 +166,48 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
     if (d2 < bd || (d2 == bd && k < bk)) { bd = d2; bk = k; }
     if (f >= -B && f <= amb && (d2 < od || (d2 == od && k < ok)) && exact(k) < 0) { od = d2; ok = k; }
   };
+  // learned proposal, outside certificate: a candidate certified closer than v_i
+  // settles "outside" with no grid scan (same exact criterion as the scan)
+  if (C.ncand > 0) {
+    T cd = T(1e30);
+    int ck = 0x7fffffff;
+    if (lane < C.ncand) {
+      int k = C.cand[(long long)i * C.ncand + lane];
+      if (k >= 0 && k != i && k != e0 && k != e1 && k != e2) {
+        T dx = C.sites[3 * k] - gx, dy = C.sites[3 * k + 1] - gy, dz = C.sites[3 * k + 2] - gz;
+        T d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 - di2 < -B) { cd = d2; ck = k; }
+      }
+    }
+    warp_argmin(cd, ck);
+    if (ck != 0x7fffffff) { *wit = ck; return 1; }
+  }
+  // learned form: when the ball of radius |q - v_i| around q lies inside the ball
+  // holding v_i's 32 nearest sites (2 |q - v_i| <= r32), every site that could be
+  // closer to q than v_i is in that list, so the list settles the test exactly
+  if (C.knn) {
+    float d32 = C.knn_d2[(long long)i * 32 + 31];
+    float r32 = d32 > 0.f ? sqrtf(d32 * (1.f - 1e-6f)) : 0.f;
+    if (C.knn[(long long)i * 32 + 31] >= 0 && (double)r32 >= 2.0 * ((double)di + (double)delta) * (1.0 + 1e-5) + 1e-30) {
+      if (lane == 0) atomicAdd(C.stats + VD_STAT_LIST_TESTS, 1ull);
+      int k = C.knn[(long long)i * 32 + lane];
+      T ld = T(1e30), lo = T(1e30);
+      int lk = 0x7fffffff, lok = 0x7fffffff;
+      if (k >= 0 && k != e0 && k != e1 && k != e2) {
+        T dx = C.sites[3 * k] - gx, dy = C.sites[3 * k + 1] - gy, dz = C.sites[3 * k + 2] - gz;
+        T d2 = dx * dx + dy * dy + dz * dz;
+        T f = d2 - di2;
+        if (f < -B) { ld = d2; lk = k; }
+        else if (f <= B && exact(k) < 0) { lo = d2; lok = k; }
+      }
+      warp_argmin(ld, lk);
+      if (lk != 0x7fffffff) { *wit = lk; return 1; }
+      warp_argmin(lo, lok);
+      if (lok != 0x7fffffff) { *wit = lok; return 1; }
+      *wit = -1;
+      return 0;
+    }
+  }
   for (int lev = C.G.query_level(gx, gy, gz); lev >= 0; --lev) {
     int cx, cy, cz;
     C.G.cell_at(lev, gx, gy, gz, cx, cy, cz);

@@ -227,6 +227,95 @@ __global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(De
 }
 
 // ---------------------------------------------------------------------------
+// the 32 nearest other sites of every site (features of the learned proposal)
+// ---------------------------------------------------------------------------
+constexpr int KNN = 32;
+constexpr int KNN_CAP = 1024;
+constexpr int KNN_WARPS = 4;
+
+struct KnnScratch {
+  float d2[KNN_CAP];
+  int id[KNN_CAP];
+  int cnt;
+  ScanScratch ss;  // segment table of rings beyond ring 1
+};
+
+// warp per site: collect the sites of growing rings around v_i, then select the
+// 32 smallest squared distances (ties: smaller index) once the 32nd is covered
+template <typename T>
+__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(Dev<T> C, int* knn, float* knn_d2) {
+  __shared__ KnnScratch sh[KNN_WARPS];
+  KnnScratch& S = sh[threadIdx.x >> 5];
+  int lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = gw; i < C.n; i += nw) {
+    T qx = C.sites[3 * i], qy = C.sites[3 * i + 1], qz = C.sites[3 * i + 2];
+    if (lane == 0) S.cnt = 0;
+    __syncwarp();
+    auto visit = [&](const typename Prec<T>::V4& s) {
+      int k = site_id(s);
+      if (k == i) return;
+      T dx = s.x - qx, dy = s.y - qy, dz = s.z - qz;
+      int slot = atomicAdd(&S.cnt, 1);
+      if (slot < KNN_CAP) { S.d2[slot] = (float)(dx * dx + dy * dy + dz * dz); S.id[slot] = k; }
+    };
+    int lev = C.G.query_level(qx, qy, qz), cx, cy, cz;
+    C.G.cell_at(lev, qx, qy, qz, cx, cy, cz);
+    // certified: every site within `cover` of v_i was stored and at least 32 of
+    // the stored distances are below cover^2 (so no unseen site can be nearer
+    // than the 32nd); otherwise the list is kept for the features but flagged
+    bool certified = false;
+    for (int r = 1;; ++r) {
+      warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S.ss, visit);
+      __syncwarp();
+      int cnt = min(S.cnt, KNN_CAP);
+      T m = C.G.cover(lev, cx, cy, cz, r, qx, qy, qz);
+      if (S.cnt > KNN_CAP) break;
+      if (m >= T(1e29)) { certified = true; break; }
+      if (cnt >= KNN) {
+        float m2 = (float)(m * m) * (1.f - 1e-5f);
+        int below = 0;
+        for (int t = lane; t < cnt; t += 32) below += S.d2[t] <= m2;
+        below = __reduce_add_sync(FULL, below);
+        if (below >= KNN) { certified = true; break; }
+      }
+      if (r >= 4) break;
+    }
+    int cnt = min(S.cnt, KNN_CAP);
+    __syncwarp();
+    // selection of the 32 nearest, in order
+    for (int k = 0; k < KNN; ++k) {
+      float bd = 3.0e38f;
+      int bi = 0x7fffffff, bs = -1;
+      for (int t = lane; t < cnt; t += 32) {
+        float d = S.d2[t];
+        int id = S.id[t];
+        if (d < bd || (d == bd && id < bi)) { bd = d; bi = id; bs = t; }
+      }
+      float d0 = bd;
+      int i0 = bi;
+      warp_argmin(bd, bi);
+      if (d0 == bd && i0 == bi && bs >= 0) S.d2[bs] = 3.0e38f;
+      if (lane == 0) {
+        knn[(long long)i * KNN + k] = bi == 0x7fffffff ? -1 : bi;
+        // a negative 32nd distance marks a list that is not certified complete
+        knn_d2[(long long)i * KNN + k] = (k == KNN - 1 && !certified) ? -1.f : bd;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// candidates ranked by distance: the first k of the 32 nearest
+__global__ void k_cand_from_knn(int n, int k, const int* knn, int* cand) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * k) return;
+  long long i = t / k;
+  int r = (int)(t - i * k);
+  cand[t] = knn[i * KNN + r];
+}
+
+// ---------------------------------------------------------------------------
 // per-site reduction, deterministic: the pieces of a site are summed in order
 // of their simplex index whatever order the flood produced them in
 // ---------------------------------------------------------------------------

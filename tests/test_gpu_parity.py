@@ -141,3 +141,22 @@ def test_shell_1m_sampled(gpu):
     pick = np.sort(rng.choice(len(w["sites"]), 200, replace=False))
     op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
     compare_full(w, r, p, op, sites_subset=pick)
+
+
+@pytest.mark.parametrize("name,n", [("cube", 20000), ("shell", 30000)])
+def test_learned_form_equals_plain_bitwise(gpu, name, n):
+    """The learned proposal only orders and shortcuts the search; every clip is
+    still decided by the exact test and integration is canonical, so the output
+    equals the plain search's bit for bit (per-site measure, centroid, CSR)."""
+    w = I.workload(name, n=n)
+    d = None
+    from paper_2509_07175_b300 import binding as B
+    d = B.diagram_from_workload(w)
+    plain = d.compute()
+    for k in (8, 16, 32):
+        d.set_options(learned=1, topk=k, stats=1)
+        lr = d.compute()
+        assert lr["stats"]["learned_hits"] > 0
+        for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+            assert torch.equal(plain[key], lr[key]), (k, key)
+    d.close()
