@@ -31,11 +31,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "cube"
+DEFAULT_WORKLOAD = "shell"
 METRIC = "clipped Voronoi cells/sec (3D, 1M sites) learned+batched vs plain GPU, oracle-exact"
 UNIT = "cells/s"
 DESC = {
     "cube": "3D clipped VD: unit cube as 6 tets, 100,000 uniform sites (FP32, FP64-filtered signs)",
+    "cube1m": "3D clipped VD: unit cube as 6 tets, 1,000,000 uniform sites (FP32)",
     "shell": "3D clipped VD: tetrahedralised spherical shell (172,032 tets), 1,000,000 sites "
              "(16-component Gaussian mixture sigma 0.02 + 10% uniform), FP32",
     "cube2m": "3D clipped VD: unit cube as 6 tets, 2,000,000 uniform sites, FP32",
@@ -154,6 +155,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(DESC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain", action="store_true", help="time the plain search instead of the learned form")
+    ap.add_argument("--topk", type=int, default=16)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,11 +179,31 @@ def main():
     w = I.workload(args.workload, seed=None if rank == 0 else I.SEED_BASE + 1000 + rank)
     n = len(w["sites"])
     d = B.diagram_from_workload(w)
+    form = dict(learned=0 if args.plain else 1, topk=args.topk)
+    # the plain form (the paper's search alone) beside the learned+batched one:
+    # identical output, timed the same way on a few steps
+    plain_ms = None
+    if not args.plain:
+        d.set_options(timing=1, learned=0)
+        ref = d.compute()
+        pm = []
+        for _ in range(max(1, min(3, args.steps))):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            code, _r = d.compute_raw()
+            e1.record()
+            torch.cuda.synchronize()
+            pm.append(e0.elapsed_time(e1))
+        plain_ms = statistics.median(pm)
     # counters for the roofline numerator (an untimed run with the counters on)
-    d.set_options(stats=1)
+    d.set_options(stats=1, **form)
     rs = d.compute()
     counts = rs["stats"]
-    d.set_options(timing=1)
+    if not args.plain:
+        for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+            assert torch.equal(ref[key], rs[key]), f"learned form differs from plain in {key}"
+    d.set_options(timing=1, **form)
     for _ in range(args.warmup):
         code, _r = d.compute_raw()
         assert code == 0, B.ERRORS.get(code, code)
@@ -228,7 +251,7 @@ def main():
     off_h = torch.empty(n + 1, dtype=torch.int64).pin_memory()
     nnz = int(rs["nbr_off"][-1].item())
     idx_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
-    d.set_options()
+    d.set_options(**form)
     for _ in range(2):
         d.update_sites_host(host_sites)
         d.compute_raw()
@@ -265,7 +288,8 @@ def main():
         pass
     max_mhz = ck.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
     peak_tflops = sm * 128 * 2 * max_mhz * 1e6 / 1e12
-    flops = 8.0 * counts["sites_scanned"]
+    # 8 FLOP per site-distance evaluation: grid scans plus the 32-site list tests
+    flops = 8.0 * (counts["sites_scanned"] + 32 * counts.get("list_tests", 0))
     clip_s = statistics.median(clip_ms) / 1e3 if clip_ms else float("nan")
     achieved = flops / clip_s / 1e12
     line = {
@@ -285,8 +309,14 @@ def main():
         "gpu_launches": launches,
         "clocks": ck,
         "stats": {k: counts[k] for k in ("nn_queries", "corner_tests", "clips", "lambda_steps", "search_steps",
-                                         "fp64", "uncertain", "ties", "sites_scanned", "fallback")},
+                                         "fp64", "uncertain", "ties", "sites_scanned", "fallback", "learned_hits",
+                                         "list_tests")},
+        "form": ("plain (Sec. 3.2 / 5.1 search)" if args.plain else
+                 f"learned+batched (32-NN candidates, top-{args.topk}; output bit-identical to plain)"),
     }
+    if plain_ms is not None:
+        line["plain"] = {"value": n / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
+                         "speedup_learned_over_plain": plain_ms / (total_ms / args.steps)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     d.close()

@@ -77,7 +77,7 @@ struct vd_ctx {
   int ncand = 0;
   int* knn = nullptr;             // [n*32] nearest sites (learned proposal)
   float* knn_d2 = nullptr;
-  int* lcand = nullptr;           // [n*32] candidates computed by the library
+  unsigned* cmask = nullptr;      // [n] ranked candidates among the 32 nearest
   int flood_grid = 0;
   size_t flood_smem = 0;
   bool have_domain = false;
@@ -170,10 +170,10 @@ static Dev<T> make_dev(vd_ctx* c) {
     D.G.L[l].ih = (T)(1.0 / h);
   }
   if (c->cand) { D.cand = c->cand; D.ncand = c->ncand; }
-  else if (c->opt.learned && c->lcand) { D.cand = c->lcand; D.ncand = c->opt.topk; }
   else { D.cand = nullptr; D.ncand = 0; }
   D.knn = (c->opt.learned && !c->cand) ? c->knn : nullptr;
   D.knn_d2 = c->knn_d2;
+  D.cmask = c->cmask;
   D.hash = c->hash; D.hmask = c->hmask; D.queue = c->queue; D.qcap = c->qcap; D.ctr = c->ctr;
   D.pmeas = (T*)c->pmeas; D.pm1 = (T*)c->pm1; D.pfoff = c->pfoff; D.pfcnt = c->pfcnt; D.pflags = c->pflags;
   D.fcap = c->fcap;
@@ -248,7 +248,7 @@ static void enqueue_compute(vd_ctx* c) {
   if (c->opt.learned && !c->cand) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
     k_knn<T><<<c->nsm * 8, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
-    k_cand_from_knn<<<nblk(c->n * (long long)c->opt.topk, 256), 256, 0, s>>>((int)c->n, c->opt.topk, c->knn, c->lcand);
+    k_cand_by_distance<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->opt.topk, c->cmask);
     c->launches += 2;
   }
   mark(c, 2);
@@ -676,7 +676,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   DALLOC(c->qlev, unsigned char, c->G, true);
   DALLOC(c->knn, int, n * KNN, true);
   DALLOC(c->knn_d2, float, n * KNN, true);
-  DALLOC(c->lcand, int, n * KNN, true);
+  DALLOC(c->cmask, unsigned, n, true);
   DALLOC(c->cellid, int, n, true);
   DALLOC(c->ccount, int, nbmax + 1, true);
   DALLOC(c->cstart, int, c->G + 1, true);

@@ -184,7 +184,8 @@ __device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int 
 
 // ----- one pair ------------------------------------------------------------------
 struct Counters {
-  unsigned long long nn, corner, clips, lam, search, scanned, learned, fallback;
+  unsigned nn, corner, clips, lam, search, learned, fallback, list;
+  unsigned long long scanned;
 };
 
 __device__ __forceinline__ void add_plane(Warp3& W, int slot, float4 P, float2 M, int src, int lane) {
@@ -207,26 +208,24 @@ __device__ __noinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, flo
 // nearest site of the search point v_i + s.  Learned form: when 2|s| <= r32 the
 // nearest site is v_i or one of v_i's 32 nearest sites (any site at least as close
 // to the point as v_i lies within 2|s| of v_i), found with no grid scan.
-__device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, int i, float3 vi, float sx, float sy,
-                                         float sz, int lane, Counters& K) {
+__device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const NbrList<float>& L, int i, float3 vi,
+                                         float sx, float sy, float sz, int lane, Counters& K) {
   float px = vi.x + sx, py = vi.y + sy, pz = vi.z + sz;
-  if (C.knn && C.knn[(long long)i * 32 + 31] >= 0 && C.knn_d2[(long long)i * 32 + 31] > 0.f) {
-    float r32 = sqrtf(C.knn_d2[(long long)i * 32 + 31] * (1.f - 1e-6f));
+  if (L.r32 > 0.f) {
     float s = sqrtf(sx * sx + sy * sy + sz * sz);
-    if (2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= r32) {
-      int k = C.knn[(long long)i * 32 + lane];
+    if (2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= L.r32) {
       float d2 = 1e30f;
       int kk = 0x7fffffff;
-      if (k >= 0) {
-        float dx = C.sites[3 * k] - px, dy = C.sites[3 * k + 1] - py, dz = C.sites[3 * k + 2] - pz;
+      if (L.id >= 0) {
+        float dx = L.x - px, dy = L.y - py, dz = L.z - pz;
         d2 = dx * dx + dy * dy + dz * dz;
-        kk = k;
+        kk = L.id;
       }
       float dxi = vi.x - px, dyi = vi.y - py, dzi = vi.z - pz;
       float di2 = dxi * dxi + dyi * dyi + dzi * dzi;
       if (lane == 0 && (di2 < d2 || (di2 == d2 && i < kk))) { d2 = di2; kk = i; }
       warp_argmin(d2, kk);
-      if (lane == 0) atomicAdd(C.stats + VD_STAT_LIST_TESTS, 1ull);
+      K.list++;
       K.nn++;
       return kk;
     }
@@ -236,7 +235,8 @@ __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, int i, f
 
 // Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
 // Returns the bisector site j for the outside corner t.
-__device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, float3 vi, int t, int lane, Counters& K) {
+__device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, const NbrList<float>& L, int i, float3 vi,
+                                          int t, int lane, Counters& K) {
   float4 q = W.tq[t];
   int wit = W.twit[t];
   float dist = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
@@ -244,15 +244,20 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, 
   float gx = q.x, gy = q.y, gz = q.z;
   int j = wit;
   float delta = C.delta[i];
-  if (C.ncand > 0) {
+  if (__any_sync(FULL, L.cand)) {
     // learned proposal, shortcut: the first crossing of the ray v_i -> p with a
     // candidate bisector (or the witness's); one query there either confirms it as
     // the exit point of Omega_i or restarts the plain search from it (Sec. 3.2)
     float tb = 1.f;
     int cb = 0x7fffffff;
-    int k = lane < C.ncand ? C.cand[(long long)i * C.ncand + lane] : (lane == 31 ? wit : -1);
+    // the witness joins the candidates in the lane that is not one
+    unsigned nc = __ballot_sync(FULL, L.cand);
+    int wl = nc == FULL ? -1 : __ffs(~nc) - 1;
+    int k = L.cand ? L.id : (lane == wl ? wit : -1);
     if (k >= 0 && k != i) {
-      float wx = C.sites[3 * k] - vi.x, wy = C.sites[3 * k + 1] - vi.y, wz = C.sites[3 * k + 2] - vi.z;
+      float kx = L.cand ? L.x : C.sites[3 * k], ky = L.cand ? L.y : C.sites[3 * k + 1],
+            kz = L.cand ? L.z : C.sites[3 * k + 2];
+      float wx = kx - vi.x, wy = ky - vi.y, wz = kz - vi.z;
       float den = wx * q.x + wy * q.y + wz * q.z;
       if (den > 0.f) {
         float tt = 0.5f * (wx * wx + wy * wy + wz * wz) / den;
@@ -262,7 +267,7 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, int i, 
     warp_argmin(tb, cb);
     if (cb != 0x7fffffff) {
       float sx = q.x * tb, sy = q.y * tb, sz = q.z * tb;
-      int kk = nn_search(C, W, i, vi, sx, sy, sz, lane, K);
+      int kk = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K);
       K.search++;
       if (kk == i || kk == cb) { K.learned++; return cb; }
       j = kk;
@@ -286,7 +291,7 @@ search:
     float tt = 0.5f * (wx * wx + wy * wy + wz * wz) / den;
     if (!(tt < 1.f)) return j;   // the bisector meets the segment at its end
     float sx = gx * tt, sy = gy * tt, sz = gz * tt;
-    int k = nn_search(C, W, i, vi, sx, sy, sz, lane, K);
+    int k = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K);
     K.search++;
     if (k == i || k == j) return j;
     j = k;
@@ -623,7 +628,8 @@ __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i,
 #endif
 
 __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long long slot, int lane) {
-  Counters K = {0, 0, 0, 0, 0, 0, 0, 0};
+  Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const NbrList<float> L = load_nbrs(C, i, lane);
   PROF_T0();
   float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   Masks Mk;
@@ -659,12 +665,12 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       for (int u = 0; u < 3; ++u) if (ex[u] < 0) ex[u] = -2;  // tet faces exclude no site
       auto exact = [&](int k) { return exact_side(C, W, a, i, t, k); };
       int wit;
-      int sc = 0;
-      int out = corner_outside(C, i, vi.x, vi.y, vi.z, q.x, q.y, q.z, q.w, ex, lane, W.S, W.A, exact, &wit, &sc);
+      int sc = 0, ls = 0;
+      int out = corner_outside(C, i, vi.x, vi.y, vi.z, q.x, q.y, q.z, q.w, ex, lane, W.S, L, exact, &wit, &sc, &ls);
       K.corner++;
       K.nn++;
       K.scanned += sc;
-      if (*(volatile int*)C.status) return;
+      K.list += ls;
       if (out) {
         Mk.out[t >> 5] |= 1u << (t & 31);
         if (lane == 0) W.twit[t] = wit;
@@ -677,7 +683,8 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
     PROF_ADD(1);
     if (p < 0) break;
     if (++nclip > C.max_clips) { set_error(C.status, VD_ERR_LIMIT); return; }
-    int j = find_bisector(C, W, i, vi, p, lane, K);
+    if (*(volatile int*)C.status) return;
+    int j = find_bisector(C, W, L, i, vi, p, lane, K);
     PROF_ADD(2);
     // free plane slot for B_ij
     unsigned long long freep = ~Mk.palive & ((1ull << MAXP) - 1ull);
@@ -756,6 +763,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       stat_add(C, VD_STAT_SITES_SCANNED, K.scanned);
       stat_add(C, VD_STAT_FALLBACK, K.fallback);
       stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
+      stat_add(C, VD_STAT_LIST_TESTS, K.list);
     }
   }
   __syncwarp();

@@ -182,7 +182,7 @@ __device__ __forceinline__ int side_of(const Dev<T>& C, const WarpP<T>& W, int a
 }
 
 struct Counters {
-  unsigned long long nn, corner, clips, lam, search, scanned, fallback;
+  unsigned long long nn, corner, clips, lam, search, scanned, fallback, learned, list;
 };
 
 template <typename T>
@@ -195,8 +195,36 @@ __device__ __noinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z
   return k;
 }
 
+// nearest site of v_i + s; learned form: from the 32-NN list when 2|s| <= r32
 template <typename T>
-__device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, const T* vi, int k, int lane, Counters& K) {
+__device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const NbrList<T>& L, int i, const T* vi,
+                                         T sx, T sy, T sz, int lane, Counters& K) {
+  T px = vi[0] + sx, py = vi[1] + sy, pz = vi[2] + sz;
+  if (L.r32 > 0.f) {
+    T s = sqrt(sx * sx + sy * sy + sz * sz);
+    if ((double)(T(2) * s) * (1.0 + 1e-5) + 4e-7 * (double)(fabs(px) + fabs(py) + fabs(pz)) <= (double)L.r32) {
+      T d2 = T(1e30);
+      int kk = 0x7fffffff;
+      if (L.id >= 0) {
+        T dx = L.x - px, dy = L.y - py, dz = L.z - pz;
+        d2 = dx * dx + dy * dy + dz * dz;
+        kk = L.id;
+      }
+      T dxi = vi[0] - px, dyi = vi[1] - py, dzi = vi[2] - pz;
+      T di2 = dxi * dxi + dyi * dyi + dzi * dzi;
+      if (lane == 0 && (di2 < d2 || (di2 == d2 && i < kk))) { d2 = di2; kk = i; }
+      warp_argmin(d2, kk);
+      K.nn++;
+      K.list++;
+      return kk;
+    }
+  }
+  return nn_query(C, W, px, py, pz, lane, K);
+}
+
+template <typename T>
+__device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, const NbrList<T>& L, int i, const T* vi,
+                                          int k, int lane, Counters& K) {
   typename Prec<T>::V4 q = W.vq[k];
   int wit = W.vwit[k];
   T dist = sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
@@ -204,6 +232,35 @@ __device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, c
   T gx = q.x, gy = q.y, gz = q.z;
   int j = wit;
   T delta = C.delta[i];
+  if (__any_sync(FULL, L.cand)) {
+    // learned proposal: first crossing of the ray v_i -> p with a candidate
+    // bisector (or the witness's), confirmed by one query (as in 3D)
+    T tb = T(1);
+    int cb = 0x7fffffff;
+    unsigned nc = __ballot_sync(FULL, L.cand);
+    int wl = nc == FULL ? -1 : __ffs(~nc) - 1;
+    int kc = L.cand ? L.id : (lane == wl ? wit : -1);
+    if (kc >= 0 && kc != i) {
+      T kx = L.cand ? L.x : C.sites[3 * kc], ky = L.cand ? L.y : C.sites[3 * kc + 1],
+        kz = L.cand ? L.z : C.sites[3 * kc + 2];
+      T wx = kx - vi[0], wy = ky - vi[1], wz = kz - vi[2];
+      T den = wx * q.x + wy * q.y + wz * q.z;
+      if (den > T(0)) {
+        T tt = T(0.5) * (wx * wx + wy * wy + wz * wz) / den;
+        if (tt < tb) { tb = tt; cb = kc; }
+      }
+    }
+    warp_argmin(tb, cb);
+    if (cb != 0x7fffffff) {
+      T sx = q.x * tb, sy = q.y * tb, sz = q.z * tb;
+      int kk = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K);
+      K.search++;
+      if (kk == i || kk == cb) { K.learned++; return cb; }
+      j = kk;
+      gx = sx; gy = sy; gz = sz;
+      goto search;
+    }
+  }
   for (int lam = 2; lam < 2 + C.max_lambda; ++lam) {
     T step = T(lam) * delta;
     if (!(step < dist)) break;
@@ -212,6 +269,7 @@ __device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, c
     K.lam++;
     if (kk != i) { gx = sx; gy = sy; gz = sz; j = kk; break; }
   }
+search:
   for (int s = 0; s < C.max_search; ++s) {
     T wx = C.sites[3 * j] - vi[0], wy = C.sites[3 * j + 1] - vi[1], wz = C.sites[3 * j + 2] - vi[2];
     T den = wx * gx + wy * gy + wz * gz;
@@ -219,7 +277,7 @@ __device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, int i, c
     T tt = T(0.5) * (wx * wx + wy * wy + wz * wz) / den;
     if (!(tt < T(1))) return j;
     T sx = gx * tt, sy = gy * tt, sz = gz * tt;
-    int kk = nn_query(C, W, vi[0] + sx, vi[1] + sy, vi[2] + sz, lane, K);
+    int kk = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K);
     K.search++;
     if (kk == i || kk == j) return j;
     j = kk;
@@ -273,8 +331,9 @@ __device__ __noinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int
 template <typename T>
 __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long long slot, int lane) {
   using V4 = typename Prec<T>::V4;
-  Counters K = {0, 0, 0, 0, 0, 0, 0};
+  Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T vi[3] = {C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]};
+  const NbrList<T> L = load_nbrs(C, i, lane);
   int np = 4, nv = 3;
   if (lane < 4) {
     V4 P;
@@ -308,11 +367,12 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       if (ex[1] < 0) ex[1] = -2;
       int nvv = nv, kk = k;
       auto exact = [&](int site) { return exact_side(C, W, a, i, kk, nvv, site); };
-      int wit, sc = 0;
-      int out = corner_outside(C, i, vi[0], vi[1], vi[2], q.x, q.y, q.z, q.w, ex, lane, W.S, W.A, exact, &wit, &sc);
+      int wit, sc = 0, ls = 0;
+      int out = corner_outside(C, i, vi[0], vi[1], vi[2], q.x, q.y, q.z, q.w, ex, lane, W.S, L, exact, &wit, &sc, &ls);
       K.corner++;
       K.nn++;
       K.scanned += sc;
+      K.list += ls;
       if (*(volatile int*)C.status) return;
       __syncwarp();
       if (lane == 0) { W.vst[k] = out ? 2 : 1; W.vwit[k] = wit; }
@@ -321,7 +381,7 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
     }
     if (p < 0) break;
     if (++nclip > C.max_clips) { set_error(C.status, VD_ERR_LIMIT); return; }
-    int j = find_bisector(C, W, i, vi, p, lane, K);
+    int j = find_bisector(C, W, L, i, vi, p, lane, K);
     if (np >= MAXPL) { set_error(C.status, VD_ERR_CAPACITY); return; }
     int pl = np++;
     {
@@ -438,6 +498,8 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       stat_add(C, VD_STAT_SEARCH_STEPS, K.search);
       stat_add(C, VD_STAT_SITES_SCANNED, K.scanned);
       stat_add(C, VD_STAT_FALLBACK, K.fallback);
+      stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
+      stat_add(C, VD_STAT_LIST_TESTS, K.list);
     }
   }
   __syncwarp();

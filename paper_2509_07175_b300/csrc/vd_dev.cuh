@@ -24,7 +24,8 @@ struct Dev {
   const int* cand;       // [n*ncand] candidate neighbours, -1 unused
   int ncand;             // 0: plain search (Sec. 3.2 / 5.1 only)
   const int* knn;        // [n*32] nearest other sites, ascending (learned form), or null
-  const float* knn_d2;   // [n*32] their squared distances (FP32)
+  const float* knn_d2;   // [n*32] their squared distances (FP32); 32nd < 0: list not certified
+  const unsigned* cmask; // [n] learned form: which of the 32 nearest are ranked candidates
   // pair set and queue
   unsigned long long* hash;
   unsigned long long hmask;
@@ -113,6 +114,37 @@ __device__ __forceinline__ void stat_add(const Dev<T>& C, int slot, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
+// Learned form: the 32 nearest sites of v_i, one per lane, loaded once per pair.
+// cand marks the ranked candidates; r32 (> 0) is a certified lower bound on the
+// distance from v_i to every site that is not in the list.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct NbrList {
+  int id;       // this lane's site (-1: none)
+  T x, y, z;
+  bool cand;
+  float r32;
+};
+
+template <typename T>
+__device__ __forceinline__ NbrList<T> load_nbrs(const Dev<T>& C, int i, int lane) {
+  NbrList<T> L;
+  L.id = -1; L.x = L.y = L.z = T(0); L.cand = false; L.r32 = 0.f;
+  if (C.knn) {
+    L.id = C.knn[(long long)i * 32 + lane];
+    float d32 = C.knn_d2[(long long)i * 32 + 31];
+    int k32 = C.knn[(long long)i * 32 + 31];
+    L.r32 = (d32 > 0.f && k32 >= 0) ? sqrtf(d32 * (1.f - 1e-6f)) : 0.f;
+    L.cand = L.id >= 0 && ((C.cmask[i] >> lane) & 1u);
+  } else if (C.ncand > 0) {
+    L.id = lane < C.ncand ? C.cand[(long long)i * C.ncand + lane] : -1;
+    L.cand = L.id >= 0 && L.id != i;
+  }
+  if (L.id >= 0) { L.x = C.sites[3 * L.id]; L.y = C.sites[3 * L.id + 1]; L.z = C.sites[3 * L.id + 2]; }
+  return L;
+}
+
+// ---------------------------------------------------------------------------
 // Point-in-cell test of a polytope corner (Sec. 3.1).
 //
 // q (frame of v_i) is a corner with coordinate error bound e; excl[] holds the
@@ -134,8 +166,8 @@ struct CornerScratch {
 
 template <typename T, typename Exact>
 __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx, T qy, T qz, T e,
-                              const int* excl, int lane, ScanScratch& S, CornerScratch&, Exact& exact,
-                              int* wit, int* scanned) {
+                              const int* excl, int lane, ScanScratch& S, const NbrList<T>& L, Exact& exact,
+                              int* wit, int* scanned, int* listed) {
   const T U = Prec<T>::U;
   T gx = vix + qx, gy = viy + qy, gz = viz + qz;
   T di2;
@@ -152,7 +184,7 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
   T R = di * (T(1) + T(1e-5)) + T(2) * delta + T(4) * U * gmax;
   // ill-conditioned corner: every site that could be closer goes to the exact test
   T amb = well ? B : (R * R - di2) + B;
-  if (!well && lane == 0) atomicAdd(C.stats + VD_STAT_ILLCOND, 1ull);
+  if (!well && lane == 0 && C.want_stats) atomicAdd(C.stats + VD_STAT_ILLCOND, 1ull);
   int e0 = excl[0], e1 = excl[1], e2 = excl[2];
   // minimum of the squared distance d_k^2 (>= 0) over the candidates; f = d_k^2 - d_i^2
   T bd = T(1e30), od = T(1e30);
@@ -166,47 +198,41 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
     if (d2 < bd || (d2 == bd && k < bk)) { bd = d2; bk = k; }
     if (f >= -B && f <= amb && (d2 < od || (d2 == od && k < ok)) && exact(k) < 0) { od = d2; ok = k; }
   };
-  // learned proposal, outside certificate: a candidate certified closer than v_i
-  // settles "outside" with no grid scan (same exact criterion as the scan)
-  if (C.ncand > 0) {
-    T cd = T(1e30);
-    int ck = 0x7fffffff;
-    if (lane < C.ncand) {
-      int k = C.cand[(long long)i * C.ncand + lane];
-      if (k >= 0 && k != i && k != e0 && k != e1 && k != e2) {
-        T dx = C.sites[3 * k] - gx, dy = C.sites[3 * k + 1] - gy, dz = C.sites[3 * k + 2] - gz;
-        T d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 - di2 < -B) { cd = d2; ck = k; }
-      }
-    }
-    warp_argmin(cd, ck);
-    if (ck != 0x7fffffff) { *wit = ck; return 1; }
-  }
   // learned form: when the ball of radius |q - v_i| around q lies inside the ball
   // holding v_i's 32 nearest sites (2 |q - v_i| <= r32), every site that could be
-  // closer to q than v_i is in that list, so the list settles the test exactly
-  if (C.knn) {
-    float d32 = C.knn_d2[(long long)i * 32 + 31];
-    float r32 = d32 > 0.f ? sqrtf(d32 * (1.f - 1e-6f)) : 0.f;
-    if (C.knn[(long long)i * 32 + 31] >= 0 && (double)r32 >= 2.0 * ((double)di + (double)delta) * (1.0 + 1e-5) + 1e-30) {
-      if (lane == 0) atomicAdd(C.stats + VD_STAT_LIST_TESTS, 1ull);
-      int k = C.knn[(long long)i * 32 + lane];
-      T ld = T(1e30), lo = T(1e30);
-      int lk = 0x7fffffff, lok = 0x7fffffff;
-      if (k >= 0 && k != e0 && k != e1 && k != e2) {
-        T dx = C.sites[3 * k] - gx, dy = C.sites[3 * k + 1] - gy, dz = C.sites[3 * k + 2] - gz;
-        T d2 = dx * dx + dy * dy + dz * dz;
-        T f = d2 - di2;
-        if (f < -B) { ld = d2; lk = k; }
-        else if (f <= B && exact(k) < 0) { lo = d2; lok = k; }
-      }
-      warp_argmin(ld, lk);
-      if (lk != 0x7fffffff) { *wit = lk; return 1; }
-      warp_argmin(lo, lok);
-      if (lok != 0x7fffffff) { *wit = lok; return 1; }
-      *wit = -1;
-      return 0;
+  // closer to q than v_i is in the list, which settles the test exactly
+  if (L.r32 > 0.f && (double)L.r32 >= 2.0 * ((double)di + (double)delta) * (1.0 + 1e-5) + 1e-30) {
+    *listed += 1;
+    T ld = T(1e30), lo = T(1e30);
+    int lk = 0x7fffffff, lok = 0x7fffffff;
+    int k = L.id;
+    if (k >= 0 && k != e0 && k != e1 && k != e2) {
+      T dx = L.x - gx, dy = L.y - gy, dz = L.z - gz;
+      T d2 = dx * dx + dy * dy + dz * dz;
+      T f = d2 - di2;
+      if (f < -B) { ld = d2; lk = k; }
+      else if (f <= B && exact(k) < 0) { lo = d2; lok = k; }
     }
+    warp_argmin(ld, lk);
+    if (lk != 0x7fffffff) { *wit = lk; return 1; }
+    warp_argmin(lo, lok);
+    if (lok != 0x7fffffff) { *wit = lok; return 1; }
+    *wit = -1;
+    return 0;
+  }
+  // learned proposal, outside certificate: a ranked candidate certified closer than
+  // v_i settles "outside" with no grid scan (same exact criterion as the scan)
+  if (__any_sync(FULL, L.cand)) {
+    T cd = T(1e30);
+    int ck = 0x7fffffff;
+    int k = L.id;
+    if (L.cand && k != i && k != e0 && k != e1 && k != e2) {
+      T dx = L.x - gx, dy = L.y - gy, dz = L.z - gz;
+      T d2 = dx * dx + dy * dy + dz * dz;
+      if (d2 - di2 < -B) { cd = d2; ck = k; }
+    }
+    warp_argmin(cd, ck);
+    if (ck != 0x7fffffff) { *wit = ck; *listed += 1; return 1; }
   }
   for (int lev = C.G.query_level(gx, gy, gz); lev >= 0; --lev) {
     int cx, cy, cz;

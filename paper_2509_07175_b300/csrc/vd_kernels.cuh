@@ -194,7 +194,7 @@ struct WarpOf<float, VD_MODE_3D> {
 
 constexpr int FLOOD_WARPS = 4;
 #ifndef FLOOD_MIN_BLOCKS
-#define FLOOD_MIN_BLOCKS 4
+#define FLOOD_MIN_BLOCKS 3
 #endif
 
 template <typename T, int MODE>
@@ -307,12 +307,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(Dev<T> C, int* knn, floa
 }
 
 // candidates ranked by distance: the first k of the 32 nearest
-__global__ void k_cand_from_knn(int n, int k, const int* knn, int* cand) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)n * k) return;
-  long long i = t / k;
-  int r = (int)(t - i * k);
-  cand[t] = knn[i * KNN + r];
+__global__ void k_cand_by_distance(int n, int k, unsigned* cmask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) cmask[i] = k >= 32 ? 0xffffffffu : ((1u << k) - 1u);
 }
 
 // ---------------------------------------------------------------------------

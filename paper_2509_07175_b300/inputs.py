@@ -313,10 +313,10 @@ def workload(name: str, n: int | None = None, seed: int | None = None):
         seed = SEED_BASE + 1 if seed is None else seed
         sites = uniform_sites(n, 2, seed, f32=False)
         return dict(name=name, mode=MODE_2D, sites=sites, verts=verts, simp=simp, f64=True)
-    if name in ("cube", "cube2m"):
+    if name in ("cube", "cube2m", "cube1m"):
         verts, simp = cube_6tet()
-        n = (100_000 if name == "cube" else 2_000_000) if n is None else n
-        seed = (SEED_BASE + (2 if name == "cube" else 5)) if seed is None else seed
+        n = {"cube": 100_000, "cube1m": 1_000_000, "cube2m": 2_000_000}[name] if n is None else n
+        seed = (SEED_BASE + {"cube": 2, "cube1m": 6, "cube2m": 5}[name]) if seed is None else seed
         sites = uniform_sites(n, 3, seed)
         return dict(name=name, mode=MODE_3D, sites=sites, verts=verts, simp=simp, f64=False)
     if name == "shell":

@@ -143,7 +143,7 @@ def test_shell_1m_sampled(gpu):
     compare_full(w, r, p, op, sites_subset=pick)
 
 
-@pytest.mark.parametrize("name,n", [("cube", 20000), ("shell", 30000)])
+@pytest.mark.parametrize("name,n", [("cube", 20000), ("shell", 30000), ("square", 1000), ("torus", 20000)])
 def test_learned_form_equals_plain_bitwise(gpu, name, n):
     """The learned proposal only orders and shortcuts the search; every clip is
     still decided by the exact test and integration is canonical, so the output
