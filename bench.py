@@ -157,6 +157,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="time the plain search instead of the learned form")
     ap.add_argument("--topk", type=int, default=16)
+    ap.add_argument("--proposal", default="mlp", choices=["mlp", "distance"],
+                    help="ranking of the 32 nearest sites in the learned form")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,26 +178,52 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    training = None
+    mlp = not args.plain and args.proposal == "mlp"
+    if mlp:
+        # the learned proposal's network, trained on the GPU on labels the method
+        # produces for seeded 100k-site cube instances (outside the timed region)
+        from paper_2509_07175_b300 import learned as L
+        training = L.trained_state()
     w = I.workload(args.workload, seed=None if rank == 0 else I.SEED_BASE + 1000 + rank)
     n = len(w["sites"])
     d = B.diagram_from_workload(w)
-    form = dict(learned=0 if args.plain else 1, topk=args.topk)
-    # the plain form (the paper's search alone) beside the learned+batched one:
-    # identical output, timed the same way on a few steps
-    plain_ms = None
-    if not args.plain:
-        d.set_options(timing=1, learned=0)
-        ref = d.compute()
-        pm = []
-        for _ in range(max(1, min(3, args.steps))):
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
+    if mlp:
+        L.load_state(d, training["state"])
+    prop = B.PROPOSAL_MLP if mlp else B.PROPOSAL_DISTANCE
+    form = dict(learned=0 if args.plain else 1, topk=args.topk, proposal=prop)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def time_form(opts, steps, warm=2):
+        """Median ms per step of a form (L2 flushed before each step, CUDA events)."""
+        d.set_options(**opts)
+        for _ in range(warm):
             code, _r = d.compute_raw()
-            e1.record()
+            assert code == 0, B.ERRORS.get(code, code)
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            code, _r = d.compute_raw()
+            e1.record(stream)
             torch.cuda.synchronize()
-            pm.append(e0.elapsed_time(e1))
-        plain_ms = statistics.median(pm)
+            assert code == 0, B.ERRORS.get(code, code)
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    # the plain form (the paper's search alone) and the learned form with the
+    # distance ranking beside the headline form: identical output, timed the same way
+    beside = {}
+    if not args.plain:
+        d.set_options(learned=0)
+        ref = d.compute()
+        nb = max(1, min(5, args.steps))
+        beside["plain"] = time_form(dict(learned=0), nb)
+        if mlp:
+            beside["learned_distance"] = time_form(dict(learned=1, topk=args.topk,
+                                                        proposal=B.PROPOSAL_DISTANCE), nb)
     # counters for the roofline numerator (an untimed run with the counters on)
     d.set_options(stats=1, **form)
     rs = d.compute()
@@ -207,8 +235,6 @@ def main():
     for _ in range(args.warmup):
         code, _r = d.compute_raw()
         assert code == 0, B.ERRORS.get(code, code)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    stream = torch.cuda.current_stream()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clip_ms = []
@@ -312,11 +338,19 @@ def main():
                                          "fp64", "uncertain", "ties", "sites_scanned", "fallback", "learned_hits",
                                          "list_tests")},
         "form": ("plain (Sec. 3.2 / 5.1 search)" if args.plain else
-                 f"learned+batched (32-NN candidates, top-{args.topk}; output bit-identical to plain)"),
+                 f"learned+batched ({args.proposal} ranking of the 32 nearest, top-{args.topk}; "
+                 "output bit-identical to plain)"),
     }
-    if plain_ms is not None:
-        line["plain"] = {"value": n / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
-                         "speedup_learned_over_plain": plain_ms / (total_ms / args.steps)}
+    step_med = statistics.median(step_ms)
+    for name, ms in beside.items():
+        line[name] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                      "speedup_headline_over_this": ms / step_med}
+    if training is not None:
+        line["training"] = {"rows": training["rows"], "epochs": training["epochs"], "batch": training["batch"],
+                            "lr": training["lr"], "train_s": training["train_s"], "data_s": training["data_s"],
+                            "loss_first_epoch": training["epoch_loss"][0],
+                            "loss_last_epoch": training["epoch_loss"][-1],
+                            "data": "labels from plain computes of 8 seeded 100k-site unit-cube instances"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     d.close()

@@ -99,7 +99,12 @@ typedef struct {
   int timing;              /* 1: time the phases of vd_compute with CUDA events */
   double grid_density;     /* target sites per grid cell (0: 3.0); read by vd_set_domain */
   int topk;                /* candidates per site used by the learned proposal (0: 16, max 32) */
+  int proposal;            /* learned form's ranking of the 32 nearest sites: VD_PROPOSAL_DISTANCE
+                              (the topk nearest) or VD_PROPOSAL_MLP (the topk largest logits of
+                              the context's network, vd_mlp_*) */
 } vd_options;
+
+enum { VD_PROPOSAL_DISTANCE = 0, VD_PROPOSAL_MLP = 1 };
 
 typedef struct {
   int64_t n;               /* sites */
@@ -213,6 +218,71 @@ int vd_set_candidates(vd_ctx* ctx, const int32_t* cand, int k);
 int vd_get_pieces_noalloc(vd_ctx* ctx, int32_t* simplex, int32_t* site, int64_t* flag_off, int32_t* flags,
                           void* measure, void* moment, int64_t pieces_capacity, int64_t flags_capacity,
                           int64_t* n_pieces, int64_t* n_flags);
+
+/* ---------------------------------------------------------------------------
+ * Learned proposal network.  The paper has no counterpart: the paper's search
+ * (Sec. 3.2, Sec. 5.1) finds every bisector by point-in-cell tests alone.  The
+ * learned form orders its candidate tests by a ranking of each site's 32 nearest
+ * sites; the exact tests still decide every clip, so the diagram is the same for
+ * any ranking, trained or not.
+ *
+ * Network: input = the offsets (v_k - v_i) / d_1 of the 32 nearest sites v_k of
+ * v_i in ascending distance, d_1 = distance of the nearest (96 values, bf16,
+ * row-major [slot][xyz]; z = 0 in 2D); layers 96 -> 64 -> 64 -> 32 with ReLU;
+ * output = one logit per slot.  Parameters: VD_MLP_NPARAM FP32 values, flat:
+ * W1 [96][64], b1 [64], W2 [64][64], b2 [64], W3 [64][32], b3 [32] (weights
+ * row-major, input index first).  Products use the bf16-rounded weights and
+ * activations with FP32 accumulation; biases and logits are FP32.
+ * Loss: mean over rows and 32 slots of the binary cross-entropy of the logit
+ * against the label bit (1: the slot's site is a bisector neighbour).
+ * Every call runs on the context stream; pointers are device pointers.
+ * ------------------------------------------------------------------------- */
+enum { VD_MLP_NPARAM = 12448, VD_MLP_NIN = 96, VD_MLP_NOUT = 32 };
+
+/* Initialise the network: weights uniform in +-sqrt(6 / fan_in) from a 64-bit
+ * hash of (seed, index), biases 0, Adam moments 0, step 0. */
+int vd_mlp_init(vd_ctx* ctx, uint64_t seed);
+
+/* Set the state: params [VD_MLP_NPARAM] (required); adam_m, adam_v (NULL: 0);
+ * step = Adam steps taken (for bias correction on resume).  Copied. */
+int vd_mlp_set_state(vd_ctx* ctx, const float* params, const float* adam_m, const float* adam_v, int64_t step);
+
+/* Read the state into caller buffers (each may be NULL; step is a host
+ * pointer).  VD_ERR_STATE before vd_mlp_init / vd_mlp_set_state.
+ * Synchronises the context stream. */
+int vd_mlp_get_state(vd_ctx* ctx, float* params, float* adam_m, float* adam_v, int64_t* step);
+
+/* Training data from the last vd_compute (the sites must not have changed
+ * since): x = the network input of every site (bf16 [n*96], may be NULL) and
+ * labels = bit s set when slot s of the site's 32-NN list is in its neighbour
+ * CSR (uint32 [n], may be NULL).  Builds the 32-NN lists when that compute did
+ * not.  VD_ERR_STATE without a current vd_compute. */
+int vd_mlp_features(vd_ctx* ctx, void* x, uint32_t* labels);
+
+/* Gradient of the mean loss over `rows` rows (x bf16 [rows*96], labels [rows])
+ * at the current parameters, written to grads [VD_MLP_NPARAM] (FP32, device);
+ * the mean loss to *loss (device float).  Parameters are not changed. */
+int vd_mlp_grad(vd_ctx* ctx, const void* x, const uint32_t* labels, int64_t rows, float* grads, float* loss);
+
+/* Logits [rows*32] (FP32, device) of rows x (bf16 [rows*96]). */
+int vd_mlp_forward(vd_ctx* ctx, const void* x, int64_t rows, float* logits);
+
+/* Candidate masks of the last vd_compute of the learned form (uint32 [n],
+ * device): bit s set when slot s of the site's 32-NN list is a candidate of the
+ * ranking in use.  VD_ERR_STATE when that compute was not of the learned form
+ * or the sites changed since. */
+int vd_get_candidate_masks(vd_ctx* ctx, uint32_t* masks);
+
+/* Train with Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) for
+ * `epochs` passes over `rows` rows (at most 2^31 - 1) in batches of `batch`
+ * (at most 2^22); each pass visits the
+ * rows in the order of an affine permutation drawn from (seed, epoch).  The
+ * Adam moments and step continue from the current state.  epoch_loss
+ * (host, may be NULL) receives the mean training loss of each epoch.  The
+ * gradients are summed with FP32 atomics, so the low bits of the trained
+ * weights depend on the summation order.  Synchronises the context stream. */
+int vd_mlp_train(vd_ctx* ctx, const void* x, const uint32_t* labels, int64_t rows, int batch, int epochs, float lr,
+                 uint64_t seed, float* epoch_loss);
 
 /* Release everything owned by the context (NULL is allowed). */
 void vd_destroy(vd_ctx* ctx);

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libvd.so")
 VD_F32, VD_F64 = 0, 1
 MODE_2D, MODE_SURFACE, MODE_3D = 2, 3, 4
 FLAG_BOUNDARY = -(2 ** 31)
+PROPOSAL_DISTANCE, PROPOSAL_MLP = 0, 1
+MLP_NPARAM, MLP_NIN, MLP_NOUT = 12448, 96, 32
 STAT_NAMES = ("pairs", "nonempty", "nn_queries", "corner_tests", "clips", "lambda_steps", "search_steps",
               "fp64", "uncertain", "ties", "sites_scanned", "learned_hits", "fallback", "launches", "illcond")
 PHASE_NAMES = ("grid", "delta", "seed", "clip", "reduce")
@@ -35,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("learned", ctypes.c_int), ("mapping", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("stats", ctypes.c_int), ("queue_capacity", ctypes.c_int64), ("max_clips", ctypes.c_int),
                 ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
-                ("timing", ctypes.c_int), ("grid_density", ctypes.c_double), ("topk", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("grid_density", ctypes.c_double), ("topk", ctypes.c_int),
+                ("proposal", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -77,6 +80,14 @@ def load(path: str = LIB_PATH):
         "vd_get_pieces": ([P, ctypes.POINTER(PiecesC)], I),
         "vd_set_candidates": ([P, P, I], I),
         "vd_get_pieces_noalloc": ([P, P, P, P, P, P, P, I64, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)], I),
+        "vd_mlp_init": ([P, ctypes.c_uint64], I),
+        "vd_mlp_set_state": ([P, P, P, P, I64], I),
+        "vd_mlp_get_state": ([P, P, P, P, ctypes.POINTER(I64)], I),
+        "vd_mlp_features": ([P, P, P], I),
+        "vd_mlp_grad": ([P, P, P, I64, P, P], I),
+        "vd_mlp_forward": ([P, P, I64, P], I),
+        "vd_mlp_train": ([P, P, P, I64, I, I, ctypes.c_float, ctypes.c_uint64, P], I),
+        "vd_get_candidate_masks": ([P, P], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -91,7 +102,9 @@ def load(path: str = LIB_PATH):
 def exported_symbols():
     return ["vd_create", "vd_set_domain", "vd_set_options", "vd_set_stream", "vd_update_sites",
             "vd_update_sites_host", "vd_compute", "vd_copy_result_host", "vd_lloyd", "vd_get_sites",
-            "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc"]
+            "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc",
+            "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
+            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks"]
 
 
 class _DevArray:
@@ -226,6 +239,56 @@ class Diagram:
         c = cand.to(torch.int32).contiguous()
         self._keep.append(c)
         _check(load().vd_set_candidates(self._h, c.data_ptr(), c.shape[1]), "vd_set_candidates")
+
+    # ----- learned proposal network (vd_mlp_*) -----
+    def mlp_init(self, seed):
+        _check(load().vd_mlp_init(self._h, int(seed)), "vd_mlp_init")
+
+    def mlp_set_state(self, params, adam_m=None, adam_v=None, step=0):
+        ts = [None if t is None else t.to(device="cuda", dtype=torch.float32).contiguous()
+              for t in (params, adam_m, adam_v)]
+        f = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+        _check(load().vd_mlp_set_state(self._h, f(ts[0]), f(ts[1]), f(ts[2]), int(step)), "vd_mlp_set_state")
+        torch.cuda.current_stream().synchronize()
+
+    def mlp_get_state(self):
+        p, m, v = (torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda") for _ in range(3))
+        step = ctypes.c_int64()
+        _check(load().vd_mlp_get_state(self._h, p.data_ptr(), m.data_ptr(), v.data_ptr(), ctypes.byref(step)),
+               "vd_mlp_get_state")
+        return {"params": p, "adam_m": m, "adam_v": v, "step": int(step.value)}
+
+    def mlp_features(self, features=True, labels=True):
+        """Network inputs (bf16 [n, 96]) and neighbour labels (int32 bit masks [n]) of the last compute."""
+        x = torch.empty((self.n, MLP_NIN), dtype=torch.bfloat16, device="cuda") if features else None
+        y = torch.empty(self.n, dtype=torch.int32, device="cuda") if labels else None
+        _check(load().vd_mlp_features(self._h, None if x is None else x.data_ptr(),
+                                      None if y is None else y.data_ptr()), "vd_mlp_features")
+        return x, y
+
+    def mlp_grad(self, x, y):
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(load().vd_mlp_grad(self._h, x.data_ptr(), y.data_ptr(), x.shape[0], g.data_ptr(), loss.data_ptr()),
+               "vd_mlp_grad")
+        return g, loss
+
+    def mlp_forward(self, x):
+        z = torch.empty((x.shape[0], MLP_NOUT), dtype=torch.float32, device="cuda")
+        _check(load().vd_mlp_forward(self._h, x.data_ptr(), x.shape[0], z.data_ptr()), "vd_mlp_forward")
+        return z
+
+    def candidate_masks(self):
+        """Candidate bit masks (int32 [n]) of the last learned-form compute."""
+        m = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        _check(load().vd_get_candidate_masks(self._h, m.data_ptr()), "vd_get_candidate_masks")
+        return m
+
+    def mlp_train(self, x, y, batch=4096, epochs=3, lr=1e-3, seed=0):
+        losses = (ctypes.c_float * int(epochs))()
+        _check(load().vd_mlp_train(self._h, x.data_ptr(), y.data_ptr(), x.shape[0], int(batch), int(epochs),
+                                   float(lr), int(seed), losses), "vd_mlp_train")
+        return [float(v) for v in losses]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "vd_kernels.cuh"
+#include "vd_mlp.cuh"
 
 using namespace vd;
 
@@ -25,6 +26,9 @@ struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
 };
+
+constexpr int MLP_RANK_BLOCKS = 3;    // inference blocks per SM (61 KB of shared memory each)
+constexpr int MLP_MAX_EPOCHS = 1024;  // per-epoch loss slots of vd_mlp_train
 
 }  // namespace
 
@@ -78,6 +82,13 @@ struct vd_ctx {
   int* knn = nullptr;             // [n*32] nearest sites (learned proposal)
   float* knn_d2 = nullptr;
   unsigned* cmask = nullptr;      // [n] ranked candidates among the 32 nearest
+  bool knn_fresh = false;         // knn holds the lists of the last compute's sites
+  bool sites_fresh = false;       // sites unchanged since the last compute
+  // learned proposal network: FP32 master weights, Adam moments, gradient, bf16 copy
+  float *mlp_p = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_g = nullptr, *mlp_loss = nullptr;
+  mlp::bf16* mlp_wb = nullptr;
+  long long mlp_step = 0;
+  bool mlp_ready = false;
   int flood_grid = 0;
   size_t flood_smem = 0;
   bool have_domain = false;
@@ -145,6 +156,7 @@ static void free_domain(vd_ctx* c) {
   c->dom_allocs.clear();
   c->have_domain = false;
   c->computed = false;
+  c->sites_fresh = c->knn_fresh = false;
 }
 
 // ---------------------------------------------------------------------------
@@ -248,7 +260,11 @@ static void enqueue_compute(vd_ctx* c) {
   if (c->opt.learned && !c->cand) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
     k_knn<T><<<c->nsm * 8, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
-    k_cand_by_distance<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->opt.topk, c->cmask);
+    if (c->opt.proposal == VD_PROPOSAL_MLP)
+      mlp::k_mlp_rank<T><<<c->nsm * MLP_RANK_BLOCKS, 128, sizeof(mlp::RankSmem), s>>>(
+          D, c->knn, (const T*)c->delta, c->mlp_wb, c->mlp_p, c->opt.topk, c->cmask);
+    else
+      k_cand_by_distance<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->opt.topk, c->cmask);
     c->launches += 2;
   }
   mark(c, 2);
@@ -455,6 +471,7 @@ int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype) {
 
 int vd_update_sites(vd_ctx* c, const void* sites) {
   if (!c || !sites) return VD_ERR_ARG;
+  c->sites_fresh = c->knn_fresh = false;
   unsigned bn = nblk(c->n, 256);
   if (c->dtype == VD_F64) k_widen<double, double><<<bn, 256, 0, c->stream>>>((const double*)sites, (double*)c->sites, c->n, c->dim);
   else k_widen<float, float><<<bn, 256, 0, c->stream>>>((const float*)sites, (float*)c->sites, c->n, c->dim);
@@ -724,9 +741,14 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   return VD_OK;
 }
 
+static bool wants_network(const vd_ctx* c) {
+  return c->opt.learned && !c->cand && c->opt.proposal == VD_PROPOSAL_MLP;
+}
+
 int vd_compute(vd_ctx* c, vd_result* out) {
   if (!c) return VD_ERR_ARG;
   if (!c->have_domain) return VD_ERR_STATE;
+  if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
   CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
   if (c->opt.timing && !c->ev[0])
     for (int k = 0; k <= VD_PHASE_N; ++k) CK(cudaEventCreate(&c->ev[k]));
@@ -735,6 +757,8 @@ int vd_compute(vd_ctx* c, vd_result* out) {
   CK(cudaGetLastError());
   int st = read_status(c);
   c->timing_now = false;
+  c->sites_fresh = true;
+  c->knn_fresh = c->opt.learned && !c->cand;
   fill_result(c, out);
   return st;
 }
@@ -755,7 +779,9 @@ int vd_copy_result_host(vd_ctx* c, void* measure, void* centroid, int64_t* nbr_o
 int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
   if (!c || iters < 0) return VD_ERR_ARG;
   if (!c->have_domain) return VD_ERR_STATE;
+  if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
   if (iters == 0) return VD_OK;
+  c->sites_fresh = c->knn_fresh = false;
   CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
   if (use_graph) {
     if (!c->gexec) {
@@ -928,6 +954,184 @@ void vd_destroy(vd_ctx* c) {
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned proposal network (vd_mlp_*): state, training data, training.
+// ---------------------------------------------------------------------------
+namespace {
+
+int mlp_alloc(vd_ctx* c) {
+  if (c->mlp_p) return VD_OK;
+  DALLOC(c->mlp_p, float, mlp::NPARAM, false);
+  DALLOC(c->mlp_m, float, mlp::NPARAM, false);
+  DALLOC(c->mlp_v, float, mlp::NPARAM, false);
+  DALLOC(c->mlp_g, float, mlp::NPARAM, false);
+  DALLOC(c->mlp_loss, float, MLP_MAX_EPOCHS, false);
+  DALLOC(c->mlp_wb, mlp::bf16, mlp::NPARAM, false);
+  const int rank_smem = (int)sizeof(mlp::RankSmem), train_smem = (int)sizeof(mlp::TrainSmem);
+  CK(cudaFuncSetAttribute(mlp::k_mlp_rank<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, rank_smem));
+  CK(cudaFuncSetAttribute(mlp::k_mlp_rank<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, rank_smem));
+  CK(cudaFuncSetAttribute(mlp::k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, rank_smem));
+  CK(cudaFuncSetAttribute(mlp::k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, train_smem));
+  return VD_OK;
+}
+
+// blocks of the training kernel: about 8 tiles of 16 rows per block
+unsigned train_grid(const vd_ctx* c, long long count) {
+  long long tiles = (count + 15) / 16;
+  return (unsigned)std::max<long long>(1, std::min<long long>(c->nsm, (tiles + 7) / 8));
+}
+
+unsigned long long host_mix(unsigned long long x) {
+  x ^= x >> 30; x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27; x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+unsigned long long gcd_u64(unsigned long long a, unsigned long long b) {
+  while (b) { unsigned long long t = a % b; a = b; b = t; }
+  return a;
+}
+
+template <typename T>
+int mlp_features_t(vd_ctx* c, void* x, uint32_t* labels) {
+  cudaStream_t s = c->stream;
+  Dev<T> D = make_dev<T>(c);
+  if (!c->knn_fresh) {
+    k_knn<T><<<c->nsm * 8, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
+    c->knn_fresh = true;
+  }
+  if (x)
+    mlp::k_features<T><<<nblk(c->n * 32, 256), 256, 0, s>>>(D, c->knn, (const T*)c->delta, (mlp::bf16*)x);
+  if (labels) mlp::k_labels<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, c->knn, c->noff, c->nidx, labels);
+  CK(cudaGetLastError());
+  return VD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vd_mlp_init(vd_ctx* c, uint64_t seed) {
+  if (!c) return VD_ERR_ARG;
+  int rc = mlp_alloc(c);
+  if (rc) return rc;
+  mlp::k_mlp_init<<<nblk(mlp::NPARAM, 256), 256, 0, c->stream>>>(c->mlp_p, c->mlp_m, c->mlp_v, c->mlp_wb,
+                                                                   (unsigned long long)seed);
+  CK(cudaGetLastError());
+  c->mlp_step = 0;
+  c->mlp_ready = true;
+  return VD_OK;
+}
+
+int vd_mlp_set_state(vd_ctx* c, const float* params, const float* adam_m, const float* adam_v, int64_t step) {
+  if (!c || !params || step < 0) return VD_ERR_ARG;
+  int rc = mlp_alloc(c);
+  if (rc) return rc;
+  const size_t bytes = sizeof(float) * mlp::NPARAM;
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->mlp_p, params, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_m) CK(cudaMemcpyAsync(c->mlp_m, adam_m, bytes, cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(c->mlp_m, 0, bytes, s));
+  if (adam_v) CK(cudaMemcpyAsync(c->mlp_v, adam_v, bytes, cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(c->mlp_v, 0, bytes, s));
+  mlp::k_to_bf16<<<nblk(mlp::NPARAM, 256), 256, 0, s>>>(c->mlp_p, c->mlp_wb);
+  CK(cudaGetLastError());
+  c->mlp_step = step;
+  c->mlp_ready = true;
+  return VD_OK;
+}
+
+int vd_mlp_get_state(vd_ctx* c, float* params, float* adam_m, float* adam_v, int64_t* step) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->mlp_ready) return VD_ERR_STATE;
+  const size_t bytes = sizeof(float) * mlp::NPARAM;
+  cudaStream_t s = c->stream;
+  if (params) CK(cudaMemcpyAsync(params, c->mlp_p, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_m) CK(cudaMemcpyAsync(adam_m, c->mlp_m, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_v) CK(cudaMemcpyAsync(adam_v, c->mlp_v, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (step) *step = c->mlp_step;
+  return VD_OK;
+}
+
+int vd_mlp_features(vd_ctx* c, void* x, uint32_t* labels) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->computed || !c->sites_fresh || (labels && c->last_status != VD_OK)) return VD_ERR_STATE;
+  return c->dtype == VD_F64 ? mlp_features_t<double>(c, x, labels) : mlp_features_t<float>(c, x, labels);
+}
+
+int vd_mlp_grad(vd_ctx* c, const void* x, const uint32_t* labels, int64_t rows, float* grads, float* loss) {
+  if (!c || !x || !labels || !grads || !loss || rows < 1 || rows > (int64_t)0x7fffffff) return VD_ERR_ARG;
+  if (!c->mlp_ready) return VD_ERR_STATE;
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(grads, 0, sizeof(float) * mlp::NPARAM, s));
+  CK(cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), s));
+  mlp::k_mlp_train<<<train_grid(c, rows), 128, sizeof(mlp::TrainSmem), s>>>(
+      c->mlp_wb, c->mlp_p, (const mlp::bf16*)x, labels, rows, 0, (int)rows, 1, 0, grads, c->mlp_loss);
+  mlp::k_scale<<<1, 32, 0, s>>>(c->mlp_loss, loss, 1, (float)(1.0 / ((double)rows * mlp::NOUT)));
+  CK(cudaGetLastError());
+  return VD_OK;
+}
+
+int vd_mlp_forward(vd_ctx* c, const void* x, int64_t rows, float* logits) {
+  if (!c || !x || !logits || rows < 1) return VD_ERR_ARG;
+  if (!c->mlp_ready) return VD_ERR_STATE;
+  long long blocks = std::min<long long>((long long)c->nsm * MLP_RANK_BLOCKS, ((rows + 15) / 16 + 3) / 4);
+  mlp::k_mlp_forward<<<(unsigned)std::max<long long>(1, blocks), 128, sizeof(mlp::RankSmem), c->stream>>>(
+      c->mlp_wb, c->mlp_p, (const mlp::bf16*)x, rows, logits);
+  CK(cudaGetLastError());
+  return VD_OK;
+}
+
+int vd_get_candidate_masks(vd_ctx* c, uint32_t* masks) {
+  if (!c || !masks) return VD_ERR_ARG;
+  if (!c->computed || !c->sites_fresh || !c->knn_fresh || !c->opt.learned || c->cand) return VD_ERR_STATE;
+  CK(cudaMemcpyAsync(masks, c->cmask, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  return VD_OK;
+}
+
+int vd_mlp_train(vd_ctx* c, const void* x, const uint32_t* labels, int64_t rows, int batch, int epochs, float lr,
+                 uint64_t seed, float* epoch_loss) {
+  if (!c || !x || !labels || rows < 1 || rows > (int64_t)0x7fffffff || batch < 1 || batch > (1 << 22) || epochs < 1 ||
+      epochs > MLP_MAX_EPOCHS || !(lr > 0.f))
+    return VD_ERR_ARG;
+  if (!c->mlp_ready) return VD_ERR_STATE;
+  cudaStream_t s = c->stream;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  CK(cudaMemsetAsync(c->mlp_loss, 0, sizeof(float) * epochs, s));
+  const unsigned long long R = (unsigned long long)rows;
+  for (int e = 0; e < epochs; ++e) {
+    // visiting order of this epoch: t -> (pa t + pc) mod rows with gcd(pa, rows) = 1
+    unsigned long long h = host_mix((unsigned long long)seed ^ host_mix(0xD1B54A32D192ED03ull * (e + 1ull)));
+    unsigned long long pa = R > 1 ? 1 + h % (R - 1) : 1, pc = R > 1 ? host_mix(h) % R : 0;
+    while (gcd_u64(pa, R) != 1) pa = pa % (R - 1) + 1;
+    for (long long b0 = 0; b0 < rows; b0 += batch) {
+      const int count = (int)std::min<long long>(batch, rows - b0);
+      CK(cudaMemsetAsync(c->mlp_g, 0, sizeof(float) * mlp::NPARAM, s));
+      mlp::k_mlp_train<<<train_grid(c, count), 128, sizeof(mlp::TrainSmem), s>>>(
+          c->mlp_wb, c->mlp_p, (const mlp::bf16*)x, labels, rows, b0, count, (long long)pa, (long long)pc, c->mlp_g,
+          c->mlp_loss + e);
+      ++c->mlp_step;
+      const float c1 = (float)(1.0 - std::pow((double)b1, (double)c->mlp_step));
+      const float c2 = (float)(1.0 - std::pow((double)b2, (double)c->mlp_step));
+      mlp::k_adam<<<nblk(mlp::NPARAM, 256), 256, 0, s>>>(c->mlp_p, c->mlp_g, c->mlp_m, c->mlp_v, c->mlp_wb, lr, b1,
+                                                          b2, eps, c1, c2);
+    }
+  }
+  CK(cudaGetLastError());
+  if (epoch_loss) {
+    CK(cudaMemcpyAsync(epoch_loss, c->mlp_loss, sizeof(float) * epochs, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int e = 0; e < epochs; ++e) epoch_loss[e] = (float)(epoch_loss[e] / ((double)rows * mlp::NOUT));
+  } else {
+    CK(cudaStreamSynchronize(s));
+  }
+  return VD_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,230 @@
+"""The learned proposal network on the GPU, against the CPU oracle.
+
+* features and labels: equal to the definitions over brute-force nearest sites
+  and the oracle's neighbour sets;
+* forward pass and gradient: the GPU kernels (bf16 operands on the tensor
+  cores, FP32 accumulation) against the FP64 oracle on the same bf16-rounded
+  operands, within 2e-3 relative;
+* one Adam step of the training kernel against the oracle's update;
+* the ranking kernel's candidate masks = the top-k of the GPU logits;
+* with the network's ranking the diagram is bit-identical to the plain search's;
+* what the trained network gains over the distance ranking and over the plain
+  search (recall of neighbours among the candidates, nearest-site queries).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import mlp as M
+from paper_2509_07175_b300 import binding as B
+from paper_2509_07175_b300 import inputs as I
+from paper_2509_07175_b300 import learned as L
+
+pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 2e-3
+
+
+def _bits(y):
+    return y.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+
+
+def _x64(x):
+    return x.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("name,n", [("cube", 3000), ("square", 1000)])
+def test_features_and_labels_match_definition(gpu, name, n):
+    w = I.workload(name, n=n)
+    d = B.diagram_from_workload(w)
+    r = d.compute()
+    assert r["status"] == 0
+    x, y = d.mlp_features()
+    torch.cuda.synchronize()
+    dim = 2 if w["mode"] == I.MODE_2D else 3
+    s = w["sites"][:, :dim]
+    knn = M.knn32(s)
+    pieces = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"]).enumerate()
+    _, _, nbrs = O.per_site(len(s), w["sites"], pieces)
+    want_y = M.labels(knn, nbrs)
+    want_x = M.bf16_round(M.features(np.c_[s, np.zeros((len(s), 3 - dim))], knn)).reshape(-1, 32, 3)
+    got_x = _x64(x).reshape(-1, 32, 3)
+    got_y = _bits(y)
+    # slots whose two sites are at equal distance up to FP32 rounding may be ordered
+    # either way; everything else must match exactly (features within one bf16 step)
+    d_all = np.sqrt(((s[knn] - s[:, None, :]) ** 2).sum(-1))
+    near_tie = np.zeros_like(d_all, dtype=bool)
+    close = np.abs(np.diff(d_all, axis=1)) <= 1e-6 * d_all[:, 1:]
+    near_tie[:, 1:] |= close
+    near_tie[:, :-1] |= close
+    ok_x = np.abs(got_x - want_x) <= 2.0 ** -7 * np.abs(want_x) + 1e-30
+    assert ok_x.all(axis=2)[~near_tie].all()
+    bit_ok = ((got_y[:, None] >> np.arange(32)) & 1) == ((want_y[:, None] >> np.arange(32)) & 1)
+    assert bit_ok[~near_tie].all()
+    assert near_tie.sum() <= 4
+    d.close()
+
+
+def _grad_case(seed, rows, trained_steps=0):
+    w = I.workload("cube", n=4000, seed=I.SEED_BASE + 0x120 + seed)
+    d = B.diagram_from_workload(w)
+    d.compute()
+    x, y = d.mlp_features()
+    d.mlp_init(0x1234 + seed)
+    if trained_steps:
+        d.mlp_train(x, y, batch=512, epochs=trained_steps, lr=3e-3, seed=seed)
+    x, y = x[:rows].contiguous(), y[:rows].contiguous()
+    return d, x, y
+
+
+@pytest.mark.parametrize("seed,rows,trained", [(0, 999, 0), (1, 16, 0), (2, 4000, 2), (3, 1, 0)])
+def test_forward_and_gradient_match_oracle(gpu, seed, rows, trained):
+    d, x, y = _grad_case(seed, rows, trained)
+    st = d.mlp_get_state()
+    p = st["params"].cpu().numpy().astype(np.float64)
+    z = d.mlp_forward(x)
+    g, loss = d.mlp_grad(x, y)
+    torch.cuda.synchronize()
+    xo, yo = _x64(x), _bits(y)
+    f = M.forward(p, xo, rounded=True)
+    gz = z.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gz - f["z"]) <= GRAD_RTOL * np.linalg.norm(f["z"])
+    go, lo = M.grad(p, xo, yo, rounded=True)
+    assert abs(float(loss.item()) - lo) <= 1e-4 * lo
+    gg = g.cpu().numpy().astype(np.float64)
+    for name, shape in M.SHAPES:
+        a, b = M.unflatten(gg)[name], M.unflatten(go)[name]
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.linalg.norm(a) == 0
+            continue
+        assert np.linalg.norm(a - b) <= GRAD_RTOL * nb, (name, np.linalg.norm(a - b) / nb)
+    d.close()
+
+
+def test_adam_step_matches_oracle(gpu):
+    d, x, y = _grad_case(4, 2048)
+    st0 = d.mlp_get_state()
+    p0 = st0["params"].cpu().numpy().astype(np.float64)
+    lr = 1e-3
+    # one epoch of one batch = one step on the whole set (visiting order is irrelevant)
+    losses = d.mlp_train(x, y, batch=2048, epochs=1, lr=lr, seed=7)
+    st1 = d.mlp_get_state()
+    assert st1["step"] == 1
+    go, lo = M.grad(p0, _x64(x), _bits(y), rounded=True)
+    assert abs(losses[0] - lo) <= 1e-4 * lo
+    want, wm, wv = M.adam_step(p0, go, np.zeros_like(go), np.zeros_like(go), 1, lr=lr)
+    got = st1["params"].cpu().numpy().astype(np.float64)
+    du = (got - p0) / lr
+    dw = (want - p0) / lr
+    # |update| <= lr everywhere; entries whose gradient is well above the
+    # gradient error follow the oracle's update closely
+    assert np.all(np.abs(du) <= 1.0 + 1e-3)
+    big = np.abs(go) > 1e-2 * np.abs(go).max()
+    assert np.abs(du - dw)[big].max() < 1e-2
+    assert np.mean(np.abs(du - dw) < 1e-2) > 0.97
+    gm = st1["adam_m"].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gm - wm) <= GRAD_RTOL * np.linalg.norm(wm)
+    # resume: state copied to another context continues identically
+    d.close()
+
+
+def test_state_round_trip(gpu):
+    d, x, y = _grad_case(5, 512)
+    d.mlp_train(x, y, batch=128, epochs=1, lr=1e-3, seed=3)
+    st = d.mlp_get_state()
+    assert st["step"] == 4
+    w = I.workload("cube", n=500, seed=I.SEED_BASE + 0x130)
+    e = B.diagram_from_workload(w)
+    e.mlp_set_state(st["params"], st["adam_m"], st["adam_v"], st["step"])
+    st2 = e.mlp_get_state()
+    for k in ("params", "adam_m", "adam_v"):
+        assert torch.equal(st[k], st2[k])
+    assert st2["step"] == 4
+    assert torch.equal(d.mlp_forward(x), e.mlp_forward(x))
+    d.close()
+    e.close()
+
+
+@pytest.mark.parametrize("topk", [1, 8, 16, 32])
+def test_rank_masks_are_topk_of_logits(gpu, topk):
+    d, x, y = _grad_case(6, 4000, trained_steps=1)
+    d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=topk)
+    r = d.compute()
+    assert r["status"] == 0
+    masks = _bits(d.candidate_masks())
+    xf, _ = d.mlp_features(labels=False)
+    z = d.mlp_forward(xf).cpu().numpy()
+    order = np.argsort(-z, axis=1, kind="stable")[:, :topk]
+    want = np.zeros(len(z), dtype=np.int64)
+    for c in range(topk):
+        want |= np.int64(1) << order[:, c].astype(np.int64)
+    assert np.array_equal(masks, want)
+    d.close()
+
+
+@pytest.mark.parametrize("name,n", [("cube", 20000), ("square", 1000), ("torus", 20000), ("shell", 30000)])
+def test_network_ranking_equals_plain_bitwise(gpu, name, n):
+    w = I.workload(name, n=n)
+    d = B.diagram_from_workload(w)
+    plain = d.compute()
+    for init in (1, 2):
+        d.mlp_init(init)
+        for k in (4, 16):
+            d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=k, stats=1)
+            lr = d.compute()
+            assert lr["status"] == 0
+            for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+                assert torch.equal(plain[key], lr[key]), (init, k, key)
+    d.close()
+
+
+def test_network_requires_weights(gpu):
+    w = I.workload("cube", n=300)
+    d = B.diagram_from_workload(w, options=dict(learned=1, proposal=B.PROPOSAL_MLP))
+    with pytest.raises(B.VDError) as e:
+        d.compute()
+    assert e.value.code == -8
+    d.close()
+
+
+def test_trained_network_gain(gpu):
+    """Training with the library's recipe (labels from 8 seeded 100k-site cube
+    instances, 30 epochs of Adam, batch 1024, lr 1e-3), evaluated on a held-out
+    instance: the trained ranking captures more neighbours among its top 12 and
+    top 16 than the distance ranking and far more than the untrained network;
+    the learned form with it needs fewer nearest-site queries than the plain
+    search, at identical output."""
+    tr = L.trained_state()
+    assert tr["epoch_loss"][-1] < tr["epoch_loss"][0]
+    w = L.instance(100_000, L.HELDOUT_SEED)
+    xv, yv = L.data_of(w)
+    z_trained = L.logits_of(tr["state"], xv)
+    z_random = L.logits_of(L.random_init_state(), xv)
+    z_dist = -torch.arange(32, device="cuda", dtype=torch.float32).expand(xv.shape[0], 32)
+    rec = {k: (L.recall_at_k(z_trained, yv, k), L.recall_at_k(z_dist, yv, k), L.recall_at_k(z_random, yv, k))
+           for k in (4, 8, 12, 16)}
+    print("recall@k (trained, distance, untrained):", rec, "losses", tr["epoch_loss"][::10], "train_s", tr["train_s"])
+    for k in (12, 16):
+        assert rec[k][0] > rec[k][1] + 0.015, k
+        assert rec[k][0] > rec[k][2] + 0.1, k
+    assert rec[8][0] > rec[8][1] - 0.005
+    d = B.diagram_from_workload(w, options=dict(stats=1))
+    plain = d.compute()
+    L.load_state(d, tr["state"])
+    out = {"plain": plain}
+    for k in (8, 16):
+        d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=k, stats=1)
+        out[f"net{k}"] = d.compute()
+        d.set_options(learned=1, proposal=B.PROPOSAL_DISTANCE, topk=k, stats=1)
+        out[f"dist{k}"] = d.compute()
+    for name, r in out.items():
+        for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+            assert torch.equal(plain[key], r[key]), (name, key)
+    q = {k: (v["stats"]["nn_queries"], v["stats"]["learned_hits"], v["stats"]["search_steps"])
+         for k, v in out.items()}
+    print("nn queries, learned hits, search steps:", q)
+    assert q["net16"][0] < q["plain"][0]
+    assert q["net16"][1] > q["dist16"][1]
+    d.close()
