@@ -104,6 +104,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def replica_seed(rank: int):
+    """Seed of rank's instance: rank 0 runs the workload's own seed, every other
+    rank an independent seeded instance of the same recipe (replicas, weak scaling)."""
+    from paper_2509_07175_b300 import inputs as I
+    return None if rank == 0 else I.SEED_BASE + 1000 + rank
+
+
+def reduce_over_ranks(dist, maxes, sums, device):
+    """Element-wise MAX of `maxes` and SUM of `sums` over all ranks (no-op without
+    a process group).  Used for the step time (max over ranks) and the counts."""
+    if dist is None:
+        return list(maxes), list(sums)
+    import torch
+    tm = torch.tensor(list(maxes), dtype=torch.float64, device=device)
+    ts = torch.tensor(list(sums), dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return tm.tolist(), ts.tolist()
+
+
+def whole_job_rate(units_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Units of all ranks per second of the slowest rank."""
+    return units_per_rank * steps * world / (max_ms / 1e3)
+
+
 def cpu_baseline(w, budget_s=15.0, seed=0):
     """Oracle (FP64, all host threads) on a bounded sample of sites: cells/s."""
     import numpy as np
@@ -185,7 +210,7 @@ def main():
         # produces for seeded 100k-site cube instances (outside the timed region)
         from paper_2509_07175_b300 import learned as L
         training = L.trained_state()
-    w = I.workload(args.workload, seed=None if rank == 0 else I.SEED_BASE + 1000 + rank)
+    w = I.workload(args.workload, seed=replica_seed(rank))
     n = len(w["sites"])
     d = B.diagram_from_workload(w)
     if mlp:
@@ -258,15 +283,9 @@ def main():
         dist.barrier()
     ck = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        lt = torch.tensor([launches], device="cuda", dtype=torch.int64)
-        dist.all_reduce(lt)
-        launches = int(lt.item())
-    value = n * args.steps * world / (total_ms / 1e3)
+    (total_ms,), (launches,) = reduce_over_ranks(dist, [sum(step_ms)], [launches], "cuda")
+    launches = int(launches)
+    value = whole_job_rate(n, args.steps, world, total_ms)
 
     # end to end through the public API with host buffers
     dim = 2 if w["mode"] == B.MODE_2D else 3
@@ -292,11 +311,8 @@ def main():
         d.copy_result_host(meas_h, cen_h, off_h, idx_h)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = n * args.steps * world / e2e_s
+    (e2e_s,), _ = reduce_over_ranks(dist, [e2e_s], [], "cuda")
+    e2e_val = whole_job_rate(n, args.steps, world, e2e_s * 1e3)
     esz = 8 if w["f64"] else 4
     h2d = n * dim * esz
     d2h = n * esz + 3 * n * esz + (n + 1) * 8 + nnz * 4
