@@ -256,7 +256,10 @@ def main():
     if not args.plain:
         for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
             assert torch.equal(ref[key], rs[key]), f"learned form differs from plain in {key}"
-    d.set_options(timing=1, **form)
+    # batching: the autotuner times every clip-kernel mapping (warp / thread per pair x
+    # queue chunk) on this workload and caches the fastest for the timed steps
+    d.set_options(timing=1, mapping=0, **form)
+    tune = d.autotune()
     for _ in range(args.warmup):
         code, _r = d.compute_raw()
         assert code == 0, B.ERRORS.get(code, code)
@@ -349,6 +352,8 @@ def main():
                      "clip_share": (clip_s * 1e3) / (total_ms / args.steps), "traffic": None},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "autotune": {"choice": ("warp" if tune["mapping"] == 1 else "thread") + f" per pair, chunk {tune['chunk']}",
+                     "clip_ms_by_candidate": tune["times_ms"]},
         "clocks": ck,
         "stats": {k: counts[k] for k in ("nn_queries", "corner_tests", "clips", "lambda_steps", "search_steps",
                                          "fp64", "uncertain", "ties", "sites_scanned", "fallback", "learned_hits",

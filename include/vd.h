@@ -79,6 +79,7 @@ enum {
                                  exact tie: simplex, site, the 4 plane sources, tie flag, kind */
   VD_STAT_LIST_TESTS = 30,    /* point-in-cell tests and queries settled from the 32 nearest
                                  sites of the cell's site, with no grid scan (learned form) */
+  VD_STAT_MAPPING = 31,       /* clip-kernel mapping used: mapping | chunk << 8 (always) */
   VD_STAT_N = 32
 };
 
@@ -88,8 +89,11 @@ enum { VD_PHASE_GRID = 0, VD_PHASE_DELTA = 1, VD_PHASE_SEED = 2, VD_PHASE_CLIP =
 
 typedef struct {
   int learned;             /* 1: use the candidate lists set by vd_set_candidates */
-  int mapping;             /* 0: automatic (autotuned), 1: warp per pair, 2: half-warp per pair */
-  int chunk;               /* pairs claimed per queue access (0: automatic) */
+  int mapping;             /* clip kernel: 0 automatic (autotuned on the first compute and
+                              cached until the options or the domain change), 1 one warp per
+                              pair, 2 one thread per pair (3D FP32; other modes use 1) */
+  int chunk;               /* queue slots claimed per access (0: autotuned with mapping 0, else 1;
+                              at most 64) */
   int stats;               /* 1: collect the counters marked above */
   int64_t queue_capacity;  /* pairs (0: automatic, 8 (n + m) + 4096) */
   int max_clips;           /* clips per pair before VD_ERR_LIMIT (0: 256) */
@@ -165,6 +169,17 @@ int vd_update_sites_host(vd_ctx* ctx, const void* sites_host);
  * Synchronises the stream once at the end to read the status and counts.
  * out may be NULL.  Returns the first device-side error, if any. */
 int vd_compute(vd_ctx* ctx, vd_result* out);
+
+/* Autotune the clip kernel now on the current sites (batching, Sec. 4.3: one
+ * persistent launch drains the pair queue): runs vd_compute's work once per
+ * candidate -- one warp or one thread per pair (3D FP32), queue chunk 1 or 4
+ * (or vd_options.chunk when set) -- times the clip phase with CUDA events and
+ * caches the fastest for mapping 0.  mapping, chunk (may be NULL) receive the
+ * choice; times_ms (host float[8], may be NULL) the candidates' times in the
+ * order (warp,1), (warp,4), (thread,1), (thread,4), -1 for those not run.  All
+ * candidates compute the same diagram; the result of the last one is left as
+ * the current result.  Synchronises the context stream. */
+int vd_autotune(vd_ctx* ctx, int* mapping, int* chunk, float* times_ms);
 
 /* Copy the per-site measure [n], centroid [n*3] (context dtype) and, when
  * nbr_off is not NULL, the CSR (nbr_off [n+1] int64, nbr_idx [nnz] int32) of the

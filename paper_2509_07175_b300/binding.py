@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         "vd_mlp_forward": ([P, P, I64, P], I),
         "vd_mlp_train": ([P, P, P, I64, I, I, ctypes.c_float, ctypes.c_uint64, P], I),
         "vd_get_candidate_masks": ([P, P], I),
+        "vd_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -104,7 +105,7 @@ def exported_symbols():
             "vd_update_sites_host", "vd_compute", "vd_copy_result_host", "vd_lloyd", "vd_get_sites",
             "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc",
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
-            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks"]
+            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune"]
 
 
 class _DevArray:
@@ -198,7 +199,8 @@ class Diagram:
             "n_pieces": int(r.n_pieces),
             "stats": dict(zip(STAT_NAMES, [int(x) for x in r.stats][:len(STAT_NAMES)]),
                           error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]],
-                          list_tests=int(r.stats[30])),
+                          list_tests=int(r.stats[30]), mapping=int(r.stats[31]) & 255,
+                          chunk=int(r.stats[31]) >> 8),
             "phase_ms": dict(zip(PHASE_NAMES, [float(x) for x in r.phase_ms][:len(PHASE_NAMES)])),
         }
         return out
@@ -277,6 +279,15 @@ class Diagram:
         z = torch.empty((x.shape[0], MLP_NOUT), dtype=torch.float32, device="cuda")
         _check(load().vd_mlp_forward(self._h, x.data_ptr(), x.shape[0], z.data_ptr()), "vd_mlp_forward")
         return z
+
+    def autotune(self):
+        """Time every clip-kernel mapping on the current sites; returns the choice and the times."""
+        m, ch = ctypes.c_int(), ctypes.c_int()
+        times = (ctypes.c_float * 8)()
+        _check(load().vd_autotune(self._h, ctypes.byref(m), ctypes.byref(ch), times), "vd_autotune")
+        names = ("warp,1", "warp,4", "thread,1", "thread,4")
+        return {"mapping": m.value, "chunk": ch.value,
+                "times_ms": {nm: float(t) for nm, t in zip(names, times) if t >= 0}}
 
     def candidate_masks(self):
         """Candidate bit masks (int32 [n]) of the last learned-form compute."""

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "vd_kernels.cuh"
@@ -91,6 +92,11 @@ struct vd_ctx {
   bool mlp_ready = false;
   int flood_grid = 0;
   size_t flood_smem = 0;
+  int flood_grid_t = 0;           // thread-per-pair kernel (3D FP32)
+  int cur_mapping = 1, cur_chunk = 1;  // used by the next enqueue
+  bool tuned = false;             // autotuned choice cached for the current domain and options
+  int tuned_mapping = 1, tuned_chunk = 1;
+  float tune_ms[8] = {0};         // clip-phase time of each candidate of the last autotune
   bool have_domain = false;
   long long last_pairs = 0, last_nnz = 0, last_nonempty = 0;
   int last_status = 0;
@@ -157,6 +163,7 @@ static void free_domain(vd_ctx* c) {
   c->have_domain = false;
   c->computed = false;
   c->sites_fresh = c->knn_fresh = false;
+  c->tuned = false;
 }
 
 // ---------------------------------------------------------------------------
@@ -272,7 +279,14 @@ static void enqueue_compute(vd_ctx* c) {
   if (MODE != VD_MODE_SURFACE) k_seed_site<T><<<nblk(c->n, 128), 128, 0, s>>>(D, c->L);
   c->launches += MODE != VD_MODE_SURFACE ? 2 : 1;
   mark(c, 3);
-  k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D);
+  bool thread_form = false;
+  if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) thread_form = c->cur_mapping == 2;
+  if (thread_form) {
+    if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value)
+      k_flood_thread<<<c->flood_grid_t, FLOOD_T_THREADS, 0, s>>>(D, c->cur_chunk);
+  } else {
+    k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+  }
   c->launches += 1;
   mark(c, 4);
   cudaMemsetAsync(c->scnt, 0, sizeof(int) * (c->n + 1), s);
@@ -323,7 +337,26 @@ static int flood_config(vd_ctx* c) {
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood<T, MODE>, FLOOD_WARPS * 32, c->flood_smem));
   c->flood_grid = std::max(1, per_sm) * c->nsm;
+  c->flood_grid_t = 0;
+  if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) {
+    int per_sm_t = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_flood_thread, FLOOD_T_THREADS, 0));
+    c->flood_grid_t = std::max(1, per_sm_t) * c->nsm;
+  }
   return VD_OK;
+}
+
+// mapping of the clip kernel for the next enqueue: the caller's choice, else the
+// cached autotuned one (warp per pair with chunk 1 until tuned)
+static void resolve_mapping(vd_ctx* c) {
+  int m = c->opt.mapping, ch = c->opt.chunk;
+  if (m == 0) {
+    m = c->tuned ? c->tuned_mapping : 1;
+    if (ch <= 0) ch = c->tuned ? c->tuned_chunk : 1;
+  }
+  if (m == 2 && c->flood_grid_t == 0) m = 1;  // thread per pair: 3D FP32 only
+  c->cur_mapping = m;
+  c->cur_chunk = std::max(1, std::min(ch <= 0 ? 1 : ch, 64));
 }
 
 static int read_status(vd_ctx* c) {
@@ -348,6 +381,7 @@ static int read_status(vd_ctx* c) {
   c->last_status = st;
   c->computed = true;
   c->last_stats[VD_STAT_LAUNCHES] = (unsigned long long)c->launches;
+  c->last_stats[VD_STAT_MAPPING] = (unsigned long long)(c->cur_mapping | (c->cur_chunk << 8));
   for (int k = 0; k < VD_PHASE_N; ++k) c->last_phase_ms[k] = 0;
   if (c->timing_now) {
     const int map[5] = {VD_PHASE_GRID, VD_PHASE_DELTA, VD_PHASE_SEED, VD_PHASE_CLIP, VD_PHASE_REDUCE};
@@ -502,6 +536,7 @@ int vd_set_options(vd_ctx* c, const vd_options* o) {
   if (!c) return VD_ERR_ARG;
   c->opt = o ? *o : default_options();
   resolve_options(c->opt);
+  c->tuned = false;
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
   return VD_OK;
@@ -745,10 +780,55 @@ static bool wants_network(const vd_ctx* c) {
   return c->opt.learned && !c->cand && c->opt.proposal == VD_PROPOSAL_MLP;
 }
 
+// Autotuner of the clip kernel's mapping: runs the whole compute on the current
+// sites once per candidate (warp or thread per pair x queue chunk), times its
+// clip phase with CUDA events on the context stream and caches the fastest for
+// the current domain and options.  Every candidate produces the same diagram.
+static int autotune(vd_ctx* c) {
+  int cand_m[8], cand_c[8], nc = 0;
+  const int chunks[2] = {1, 4};
+  for (int m = 1; m <= 2; ++m) {
+    if (m == 2 && c->flood_grid_t == 0) continue;
+    if (c->opt.chunk > 0) { cand_m[nc] = m; cand_c[nc++] = std::min(c->opt.chunk, 64); continue; }
+    for (int k = 0; k < 2; ++k) { cand_m[nc] = m; cand_c[nc++] = chunks[k]; }
+  }
+  if (!c->ev[0])
+    for (int k = 0; k <= VD_PHASE_N; ++k) CK(cudaEventCreate(&c->ev[k]));
+  int best = 0;
+  double best_ms = 1e300;
+  for (int k = 0; k < 8; ++k) c->tune_ms[k] = -1.f;
+  for (int k = 0; k < nc; ++k) {
+    c->cur_mapping = cand_m[k];
+    c->cur_chunk = cand_c[k];
+    CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
+    c->timing_now = true;
+    enqueue_any(c);
+    cudaError_t e = cudaGetLastError();
+    int st = read_status(c);
+    c->timing_now = false;
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    if (st) return st;
+    double ms = c->last_phase_ms[VD_PHASE_CLIP];
+    c->tune_ms[k] = (float)ms;
+    if (ms < best_ms) { best_ms = ms; best = k; }
+  }
+  c->sites_fresh = true;
+  c->knn_fresh = c->opt.learned && !c->cand;
+  c->tuned = true;
+  c->tuned_mapping = cand_m[best];
+  c->tuned_chunk = cand_c[best];
+  return VD_OK;
+}
+
 int vd_compute(vd_ctx* c, vd_result* out) {
   if (!c) return VD_ERR_ARG;
   if (!c->have_domain) return VD_ERR_STATE;
   if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
+  if (c->opt.mapping == 0 && !c->tuned) {
+    int rc = autotune(c);
+    if (rc) return rc;
+  }
+  resolve_mapping(c);
   CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
   if (c->opt.timing && !c->ev[0])
     for (int k = 0; k <= VD_PHASE_N; ++k) CK(cudaEventCreate(&c->ev[k]));
@@ -761,6 +841,18 @@ int vd_compute(vd_ctx* c, vd_result* out) {
   c->knn_fresh = c->opt.learned && !c->cand;
   fill_result(c, out);
   return st;
+}
+
+int vd_autotune(vd_ctx* c, int* mapping, int* chunk, float* times_ms) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->have_domain) return VD_ERR_STATE;
+  if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
+  int rc = autotune(c);
+  if (rc) return rc;
+  if (mapping) *mapping = c->tuned_mapping;
+  if (chunk) *chunk = c->tuned_chunk;
+  if (times_ms) std::memcpy(times_ms, c->tune_ms, sizeof(c->tune_ms));
+  return VD_OK;
 }
 
 int vd_copy_result_host(vd_ctx* c, void* measure, void* centroid, int64_t* nbr_off, int32_t* nbr_idx) {
@@ -781,6 +873,12 @@ int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
   if (!c->have_domain) return VD_ERR_STATE;
   if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
   if (iters == 0) return VD_OK;
+  if (c->opt.mapping == 0 && !c->tuned) {
+    // tune on the current sites before any capture (the tuning computes leave the sites as they are)
+    int rc = autotune(c);
+    if (rc) return rc;
+  }
+  resolve_mapping(c);
   c->sites_fresh = c->knn_fresh = false;
   CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
   if (use_graph) {
@@ -861,6 +959,7 @@ int vd_set_candidates(vd_ctx* c, const int32_t* cand, int k) {
     c->cand = nullptr;
   }
   c->ncand = k;
+  c->tuned = false;
   if (k == 0) return VD_OK;
   int* p = nullptr;
   int rc = dalloc(c, p, (size_t)c->n * k, false);

@@ -125,7 +125,9 @@ __device__ __noinline__ ePlane eplane(const Dev<float>& C, int a, int i, int src
 // covers the rounding of the plane coefficients and of the evaluation; then
 // |q^ - q| <= (g A~ + |q| g D~) / (|D^| - g D~) + 2u|q|.  Corners whose D does
 // not clear its bound get an infinite error: every test on them is exact.
-__device__ float4 corner(float4 P0, float2 M0, float4 P1, float2 M1, float4 P2, float2 M2) {
+// (out of line: one compiled instance serves every caller, so the rounding of a
+// corner does not depend on where the compiler inlined it)
+__device__ __noinline__ float4 corner(float4 P0, float2 M0, float4 P1, float2 M1, float4 P2, float2 M2) {
   float3 x12 = make_float3(P1.y * P2.z - P1.z * P2.y, P1.z * P2.x - P1.x * P2.z, P1.x * P2.y - P1.y * P2.x);
   float3 x20 = make_float3(P2.y * P0.z - P2.z * P0.y, P2.z * P0.x - P2.x * P0.z, P2.x * P0.y - P2.y * P0.x);
   float3 x01 = make_float3(P0.y * P1.z - P0.z * P1.y, P0.z * P1.x - P0.x * P1.z, P0.x * P1.y - P0.y * P1.x);
@@ -466,6 +468,38 @@ __device__ __forceinline__ unsigned long long corner_key(int s0, int s1, int s2)
          (unsigned long long)(c & 0x1fffffu);
 }
 
+// Volume and first-moment terms of one corner A (its three edge terms, faces in
+// key order; R = reference corner of the face, B = neighbour across the edge; all
+// relative to the origin corner O).  Out of line so that every mapping of the clip
+// kernel rounds them identically.
+__device__ __noinline__ float4 corner_terms(float4 A4, float4 O, float4 R0, float4 B0, float4 R1, float4 B1,
+                                            float4 R2, float4 B2) {
+  float ax = A4.x - O.x, ay = A4.y - O.y, az = A4.z - O.z;
+  float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+  auto edge = [&](float4 R4, float4 B4) {
+    float rx = R4.x - O.x, ry = R4.y - O.y, rz = R4.z - O.z;
+    float bx = B4.x - O.x, by = B4.y - O.y, bz = B4.z - O.z;
+    float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+    float det = rx * cx + ry * cy + rz * cz;
+    v6 += det;
+    mx += det * (rx + ax + bx);
+    my += det * (ry + ay + by);
+    mz += det * (rz + az + bz);
+  };
+  edge(R0, B0);
+  edge(R1, B1);
+  edge(R2, B2);
+  return make_float4(v6, mx, my, mz);
+}
+
+// volume and first moment (frame of v_i) from the summed terms S = (6V, M_x, M_y, M_z)
+// of the corner fan around O; sigma = +-1 (orientation)
+__device__ __noinline__ float4 finish_moments(float sigma, float4 S, float4 O) {
+  float vol = sigma * S.x / 6.f;
+  float s24 = sigma / 24.f;
+  return make_float4(vol, s24 * S.y + vol * O.x, s24 * S.z + vol * O.y, s24 * S.w + vol * O.z);
+}
+
 // Integrate volume, first moment (frame of v_i) and face areas of the final
 // polytope, independently of the clip history: every corner is recomputed from
 // its three planes taken in key order (tet vertices directly from the mesh), the
@@ -550,26 +584,21 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
     for (int u = 0; u < 2; ++u)
       for (int w = 0; w < 2 - u; ++w)
         if (sr[ord[w]] > sr[ord[w + 1]]) { int tt = ord[w]; ord[w] = ord[w + 1]; ord[w + 1] = tt; }
-    float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll 1
+    float4 Rq[3], Bq[3];
+#pragma unroll
     for (int e3 = 0; e3 < 3; ++e3) {
       int e = ord[e3];
       int x = fx[e];
-      float4 R4 = W.tq[W.pref[x]], B4 = W.tq[fn[e]];
-      float rx = R4.x - O.x, ry = R4.y - O.y, rz = R4.z - O.z;
-      float bx = B4.x - O.x, by = B4.y - O.y, bz = B4.z - O.z;
-      float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-      float det = rx * cx + ry * cy + rz * cz;
-      v6 += det;
-      mx += det * (rx + ax + bx);
-      my += det * (ry + ay + by);
-      mz += det * (rz + az + bz);
+      Rq[e3] = W.tq[W.pref[x]];
+      Bq[e3] = W.tq[fn[e]];
+      float rx = Rq[e3].x - O.x, ry = Rq[e3].y - O.y, rz = Rq[e3].z - O.z;
+      float bx = Bq[e3].x - O.x, by = Bq[e3].y - O.y, bz = Bq[e3].z - O.z;
       float ux = ax - rx, uy = ay - ry, uz = az - rz, wx = bx - rx, wy = by - ry, wz = bz - rz;
       atomicAdd(&W.parea[x][0], uy * wz - uz * wy);
       atomicAdd(&W.parea[x][1], uz * wx - ux * wz);
       atomicAdd(&W.parea[x][2], ux * wy - uy * wx);
     }
-    W.contrib[rank[r]] = make_float4(v6, mx, my, mz);
+    W.contrib[rank[r]] = corner_terms(A4, O, Rq[0], Bq[0], Rq[1], Bq[1], Rq[2], Bq[2]);
   }
   __syncwarp();
   float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
@@ -583,9 +612,9 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
   }
   v6 = warp_sum(v6);
   mx = warp_sum(mx); my = warp_sum(my); mz = warp_sum(mz);
-  vol = sigma * v6 / 6.f;
-  float s24 = sigma / 24.f;
-  m1 = make_float3(s24 * mx + vol * O.x, s24 * my + vol * O.y, s24 * mz + vol * O.z);
+  float4 F = finish_moments(sigma, make_float4(v6, mx, my, mz), O);
+  vol = F.x;
+  m1 = make_float3(F.y, F.z, F.w);
   __syncwarp();
 }
 

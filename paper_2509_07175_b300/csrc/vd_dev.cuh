@@ -108,6 +108,30 @@ __device__ unsigned long long wait_item(const Dev<T>& C, long long h, int lane) 
   return __shfl_sync(FULL, key, 0);
 }
 
+// Single-thread form of wait_item (thread-per-pair kernels).
+template <typename T>
+__device__ unsigned long long wait_item_one(const Dev<T>& C, long long h) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  volatile unsigned long long* q = C.queue;
+  volatile unsigned long long* ctr = C.ctr;
+  volatile int* st = C.status;
+  for (;;) {
+    if (h < C.qcap) {
+      unsigned long long key = q[h];
+      if (key != EMPTY_KEY) return key;
+    }
+    unsigned long long done = ctr[CTR_DONE];
+    __threadfence();
+    unsigned long long tail = ctr[CTR_TAIL];
+    if (done >= tail || *st != 0) return EMPTY_KEY;
+    unsigned long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if ((long long)(t1 - t0) > C.wait_ns) { set_error(C.status, VD_ERR_LIMIT); return EMPTY_KEY; }
+    __nanosleep(256);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void stat_add(const Dev<T>& C, int slot, unsigned long long v) {
   if (v) atomicAdd(C.stats + slot, v);

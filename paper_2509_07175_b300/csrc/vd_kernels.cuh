@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "vd_clip3.cuh"
+#include "vd_clip3t.cuh"
 #include "vd_clippoly.cuh"
 
 namespace vd {
@@ -197,32 +198,84 @@ constexpr int FLOOD_WARPS = 4;
 #define FLOOD_MIN_BLOCKS 3
 #endif
 
+// Warp per pair: each warp claims `chunk` consecutive queue slots at a time.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(Dev<T> C) {
+__global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(Dev<T> C, int chunk) {
   using W = typename WarpOf<T, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W& w = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
   for (;;) {
-    unsigned long long h = 0;
-    if (lane == 0) h = atomicAdd(C.ctr + CTR_HEAD, 1ull);
-    h = __shfl_sync(FULL, h, 0);
+    unsigned long long h0 = 0;
+    if (lane == 0) h0 = atomicAdd(C.ctr + CTR_HEAD, (unsigned long long)chunk);
+    h0 = __shfl_sync(FULL, h0, 0);
+    bool stop = false;
+    for (int c = 0; c < chunk; ++c) {
+      unsigned long long h = h0 + (unsigned long long)c;
 #ifdef VD_PROFILE
-    long long tw = clock64();
+      long long tw = clock64();
 #endif
-    unsigned long long key = wait_item(C, (long long)h, lane);
+      unsigned long long key = wait_item(C, (long long)h, lane);
 #ifdef VD_PROFILE
-    if (lane == 0) atomicAdd(C.stats + 29, (unsigned long long)(clock64() - tw));
+      if (lane == 0) atomicAdd(C.stats + 29, (unsigned long long)(clock64() - tw));
 #endif
-    if (key == EMPTY_KEY) break;
-    int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
-    if constexpr (MODE == VD_MODE_3D) c3::process_pair(C, w, a, i, (long long)h, lane);
-    else cp::process_pair<T>(C, w, a, i, (long long)h, lane);
-    __syncwarp();
-    if (lane == 0) {
+      if (key == EMPTY_KEY) { stop = true; break; }
+      int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
+      if constexpr (MODE == VD_MODE_3D) c3::process_pair(C, w, a, i, (long long)h, lane);
+      else cp::process_pair<T>(C, w, a, i, (long long)h, lane);
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(C.ctr + CTR_DONE, 1ull);
+      }
+    }
+    if (stop) break;
+  }
+}
+
+// Thread per pair (3D): the threads of a warp that need work claim together
+// (one atomic for all of them), `chunk` consecutive queue slots each.
+#ifndef FLOOD_T_THREADS
+#define FLOOD_T_THREADS 128
+#endif
+#ifndef FLOOD_T_MIN_BLOCKS
+#define FLOOD_T_MIN_BLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(FLOOD_T_THREADS, FLOOD_T_MIN_BLOCKS) k_flood_thread(Dev<float> C, int chunk) {
+  c3t::Poly P;
+  c3t::Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned m = __activemask();
+    int leader = __ffs(m) - 1;
+    unsigned rank = __popc(m & ((1u << lane) - 1u));
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(C.ctr + CTR_HEAD, (unsigned long long)__popc(m) * (unsigned)chunk);
+    base = __shfl_sync(m, base, leader);
+    unsigned long long h0 = base + (unsigned long long)rank * (unsigned)chunk;
+    bool stop = false;
+    for (int c = 0; c < chunk; ++c) {
+      unsigned long long h = h0 + (unsigned long long)c;
+      unsigned long long key = wait_item_one(C, (long long)h);
+      if (key == EMPTY_KEY) { stop = true; break; }
+      int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
+      c3t::process_pair(C, P, a, i, (long long)h, K);
       __threadfence();
       atomicAdd(C.ctr + CTR_DONE, 1ull);
     }
+    if (stop) break;
+  }
+  if (C.want_stats) {
+    stat_add(C, VD_STAT_NN_QUERIES, K.nn);
+    stat_add(C, VD_STAT_CORNER_TESTS, K.corner);
+    stat_add(C, VD_STAT_CLIPS, K.clips);
+    stat_add(C, VD_STAT_LAMBDA_STEPS, K.lam);
+    stat_add(C, VD_STAT_SEARCH_STEPS, K.search);
+    stat_add(C, VD_STAT_SITES_SCANNED, K.scanned);
+    stat_add(C, VD_STAT_FALLBACK, K.fallback);
+    stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
+    stat_add(C, VD_STAT_LIST_TESTS, K.list);
   }
 }
 
