@@ -107,7 +107,7 @@ __global__ void k_query_level(int G0, const int* cstart0, unsigned char* qlev, i
 
 // delta_i = half the distance from v_i to its nearest other site (Sec. 5.1)
 template <typename T>
-__global__ void k_delta(Dev<T> C, T* delta) {
+__global__ void k_delta(const __grid_constant__ Dev<T> C, T* delta) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C.n) return;
   T d2;
@@ -120,7 +120,7 @@ __global__ void k_delta(Dev<T> C, T* delta) {
 // (simplex containing v_i, i) for every site inside the mesh
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_seed_simplex(Dev<T> C) {
+__global__ void k_seed_simplex(const __grid_constant__ Dev<T> C) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= C.m) return;
   T c[3] = {0, 0, 0};
@@ -150,7 +150,7 @@ __device__ __forceinline__ double orient2(const double* a, const double* b, cons
 }
 
 template <typename T>
-__global__ void k_seed_site(Dev<T> C, Locator L) {
+__global__ void k_seed_site(const __grid_constant__ Dev<T> C, Locator L) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C.n) return;
   double p[3] = {(double)C.sites[3 * i], (double)C.sites[3 * i + 1], (double)C.sites[3 * i + 2]};
@@ -200,7 +200,7 @@ constexpr int FLOOD_WARPS = 4;
 
 // Warp per pair: each warp claims `chunk` consecutive queue slots at a time.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(Dev<T> C, int chunk) {
+__global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(const __grid_constant__ Dev<T> C, int chunk) {
   using W = typename WarpOf<T, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W& w = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(De
 #define FLOOD_T_MIN_BLOCKS 4
 #endif
 
-__global__ void __launch_bounds__(FLOOD_T_THREADS, FLOOD_T_MIN_BLOCKS) k_flood_thread(Dev<float> C, int chunk) {
+__global__ void __launch_bounds__(FLOOD_T_THREADS, FLOOD_T_MIN_BLOCKS) k_flood_thread(const __grid_constant__ Dev<float> C, int chunk) {
   c3t::Poly P;
   c3t::Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int lane = threadIdx.x & 31;
@@ -296,7 +296,7 @@ struct KnnScratch {
 // warp per site: collect the sites of growing rings around v_i, then select the
 // 32 smallest squared distances (ties: smaller index) once the 32nd is covered
 template <typename T>
-__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(Dev<T> C, int* knn, float* knn_d2) {
+__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ Dev<T> C, int* knn, float* knn_d2) {
   __shared__ KnnScratch sh[KNN_WARPS];
   KnnScratch& S = sh[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;

@@ -156,7 +156,7 @@ struct RankSmem {
 // largest logits (equal logits: the lower slot first).  Nothing but the mask is
 // written.  4 warps per block, a tile of 16 sites per warp.
 template <typename T>
-__global__ void __launch_bounds__(128) k_mlp_rank(Dev<T> C, const int* knn, const T* delta, const bf16* wb,
+__global__ void __launch_bounds__(128) k_mlp_rank(const __grid_constant__ Dev<T> C, const int* knn, const T* delta, const bf16* wb,
                                                   const float* params, int topk, unsigned* cmask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RankSmem& SM = *reinterpret_cast<RankSmem*>(smem_raw);
