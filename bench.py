@@ -181,7 +181,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(DESC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="time the plain search instead of the learned form")
-    ap.add_argument("--topk", type=int, default=16)
+    ap.add_argument("--topk", type=int, default=24)
     ap.add_argument("--proposal", default="mlp", choices=["mlp", "distance"],
                     help="ranking of the 32 nearest sites in the learned form")
     args = ap.parse_args()

@@ -102,7 +102,7 @@ typedef struct {
   double wait_limit_s;     /* longest wait of an idle worker on the queue (0: 10 s) */
   int timing;              /* 1: time the phases of vd_compute with CUDA events */
   double grid_density;     /* target sites per grid cell (0: 3.0); read by vd_set_domain */
-  int topk;                /* candidates per site used by the learned proposal (0: 16, max 32) */
+  int topk;                /* candidates per site used by the learned proposal (0: 24, max 32) */
   int proposal;            /* learned form's ranking of the 32 nearest sites: VD_PROPOSAL_DISTANCE
                               (the topk nearest) or VD_PROPOSAL_MLP (the topk largest logits of
                               the context's network, vd_mlp_*) */

@@ -130,7 +130,7 @@ static void resolve_options(vd_options& o) {
   if (o.max_clips <= 0) o.max_clips = 256;
   if (o.max_search <= 0) o.max_search = 256;
   if (o.max_lambda <= 0) o.max_lambda = 64;
-  if (o.topk <= 0) o.topk = 16;
+  if (o.topk <= 0) o.topk = 24;
   if (o.topk > 32) o.topk = 32;
   if (!(o.wait_limit_s > 0)) o.wait_limit_s = 10.0;
 }

@@ -26,7 +26,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=None, help="sites (default: the workload's own)")
     ap.add_argument("--form", default="learned", choices=["plain", "learned"])
     ap.add_argument("--proposal", default="distance", choices=["distance", "mlp"])
-    ap.add_argument("--topk", type=int, default=16)
+    ap.add_argument("--topk", type=int, default=24)
     ap.add_argument("--mapping", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--chunk", type=int, default=1)
     ap.add_argument("--train-epochs", type=int, default=None)
