@@ -125,22 +125,38 @@ __device__ __noinline__ ePlane eplane(const Dev<float>& C, int a, int i, int src
 // covers the rounding of the plane coefficients and of the evaluation; then
 // |q^ - q| <= (g A~ + |q| g D~) / (|D^| - g D~) + 2u|q|.  Corners whose D does
 // not clear its bound get an infinite error: every test on them is exact.
-// (out of line: one compiled instance serves every caller, so the rounding of a
-// corner does not depend on where the compiler inlined it)
-__device__ __noinline__ float4 corner(float4 P0, float2 M0, float4 P1, float2 M1, float4 P2, float2 M2) {
-  float3 x12 = make_float3(P1.y * P2.z - P1.z * P2.y, P1.z * P2.x - P1.x * P2.z, P1.x * P2.y - P1.y * P2.x);
-  float3 x20 = make_float3(P2.y * P0.z - P2.z * P0.y, P2.z * P0.x - P2.x * P0.z, P2.x * P0.y - P2.y * P0.x);
-  float3 x01 = make_float3(P0.y * P1.z - P0.z * P1.y, P0.z * P1.x - P0.x * P1.z, P0.x * P1.y - P0.y * P1.x);
-  float D = P0.x * x12.x + P0.y * x12.y + P0.z * x12.z;
-  float qx = (P0.w * x12.x + P1.w * x20.x + P2.w * x01.x) / D;
-  float qy = (P0.w * x12.y + P1.w * x20.y + P2.w * x01.y) / D;
-  float qz = (P0.w * x12.z + P1.w * x20.z + P2.w * x01.z) / D;
-  float Dm = M0.x * M1.x * M2.x;
-  float Am = M0.y * M1.x * M2.x + M1.y * M2.x * M0.x + M2.y * M0.x * M1.x;
+// Every operation is an explicitly rounded intrinsic (no contraction into fused
+// multiply-adds), so each call site rounds a corner identically whatever the
+// compiler inlines around it.
+__device__ __forceinline__ float4 corner(float4 P0, float2 M0, float4 P1, float2 M1, float4 P2, float2 M2) {
+  auto cr = [](float ay, float az, float by, float bz) { return __fsub_rn(__fmul_rn(ay, bz), __fmul_rn(az, by)); };
+  auto dot = [](float ax, float ay, float az, float bx, float by, float bz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(ax, bx), __fmul_rn(ay, by)), __fmul_rn(az, bz));
+  };
+  float3 x12 = make_float3(cr(P1.y, P1.z, P2.y, P2.z), cr(P1.z, P1.x, P2.z, P2.x), cr(P1.x, P1.y, P2.x, P2.y));
+  float3 x20 = make_float3(cr(P2.y, P2.z, P0.y, P0.z), cr(P2.z, P2.x, P0.z, P0.x), cr(P2.x, P2.y, P0.x, P0.y));
+  float3 x01 = make_float3(cr(P0.y, P0.z, P1.y, P1.z), cr(P0.z, P0.x, P1.z, P1.x), cr(P0.x, P0.y, P1.x, P1.y));
+  float D = dot(P0.x, P0.y, P0.z, x12.x, x12.y, x12.z);
+  float qx = __fdiv_rn(dot(P0.w, P1.w, P2.w, x12.x, x20.x, x01.x), D);
+  float qy = __fdiv_rn(dot(P0.w, P1.w, P2.w, x12.y, x20.y, x01.y), D);
+  float qz = __fdiv_rn(dot(P0.w, P1.w, P2.w, x12.z, x20.z, x01.z), D);
+  float Dm = __fmul_rn(__fmul_rn(M0.x, M1.x), M2.x);
+  float Am = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(M0.y, M1.x), M2.x), __fmul_rn(__fmul_rn(M1.y, M2.x), M0.x)),
+                       __fmul_rn(__fmul_rn(M2.y, M0.x), M1.x));
   float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
-  float den = fabsf(D) - GAMMA * Dm;
-  float e = (den > GAMMA * Dm && isfinite(qm)) ? (GAMMA * Am + qm * GAMMA * Dm) / den + 2.f * U * qm : 1e30f;
+  float gD = __fmul_rn(GAMMA, Dm);
+  float den = __fsub_rn(fabsf(D), gD);
+  float e = (den > gD && isfinite(qm))
+                ? __fadd_rn(__fdiv_rn(__fadd_rn(__fmul_rn(GAMMA, Am), __fmul_rn(qm, gD)), den), __fmul_rn(2.f * U, qm))
+                : 1e30f;
   return make_float4(qx, qy, qz, e);
+}
+
+// A corner whose FP32 error bound exceeds 3e-3 |q| is recomputed in float64 (the
+// test is explicitly rounded so that every mapping takes the same decision).
+__device__ __forceinline__ bool loose(float4 q) {
+  float n2 = __fadd_rn(__fadd_rn(__fmul_rn(q.x, q.x), __fmul_rn(q.y, q.y)), __fmul_rn(q.z, q.z));
+  return !(q.w <= __fmul_rn(3e-3f, __fsqrt_rn(n2)));
 }
 
 // loose FP32 bound: recompute the corner from its exact planes in float64
@@ -387,7 +403,7 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
     else if (uv.z == y && uv.x == x) W.tn[u].z = (unsigned char)sl;
     else bad = true;
     float4 qc = corner(W.pn[x], W.pm[x], W.pn[y], W.pm[y], Pn, Mn);
-    if (!(qc.w <= 3e-3f * sqrtf(qc.x * qc.x + qc.y * qc.y + qc.z * qc.z)))
+    if (loose(qc))
       qc = refine64(C, a, i, W.psrc[x], W.psrc[y], W.psrc[pl]);
     W.tq[sl] = qc;
     W.twit[sl] = -1;
@@ -470,21 +486,23 @@ __device__ __forceinline__ unsigned long long corner_key(int s0, int s1, int s2)
 
 // Volume and first-moment terms of one corner A (its three edge terms, faces in
 // key order; R = reference corner of the face, B = neighbour across the edge; all
-// relative to the origin corner O).  Out of line so that every mapping of the clip
-// kernel rounds them identically.
-__device__ __noinline__ float4 corner_terms(float4 A4, float4 O, float4 R0, float4 B0, float4 R1, float4 B1,
-                                            float4 R2, float4 B2) {
-  float ax = A4.x - O.x, ay = A4.y - O.y, az = A4.z - O.z;
+// relative to the origin corner O).  Explicitly rounded operations, so every
+// mapping of the clip kernel rounds them identically.
+__device__ __forceinline__ float4 corner_terms(float4 A4, float4 O, float4 R0, float4 B0, float4 R1, float4 B1,
+                                               float4 R2, float4 B2) {
+  float ax = __fsub_rn(A4.x, O.x), ay = __fsub_rn(A4.y, O.y), az = __fsub_rn(A4.z, O.z);
   float v6 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
   auto edge = [&](float4 R4, float4 B4) {
-    float rx = R4.x - O.x, ry = R4.y - O.y, rz = R4.z - O.z;
-    float bx = B4.x - O.x, by = B4.y - O.y, bz = B4.z - O.z;
-    float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-    float det = rx * cx + ry * cy + rz * cz;
-    v6 += det;
-    mx += det * (rx + ax + bx);
-    my += det * (ry + ay + by);
-    mz += det * (rz + az + bz);
+    float rx = __fsub_rn(R4.x, O.x), ry = __fsub_rn(R4.y, O.y), rz = __fsub_rn(R4.z, O.z);
+    float bx = __fsub_rn(B4.x, O.x), by = __fsub_rn(B4.y, O.y), bz = __fsub_rn(B4.z, O.z);
+    float cx = __fsub_rn(__fmul_rn(ay, bz), __fmul_rn(az, by));
+    float cy = __fsub_rn(__fmul_rn(az, bx), __fmul_rn(ax, bz));
+    float cz = __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
+    float det = __fadd_rn(__fadd_rn(__fmul_rn(rx, cx), __fmul_rn(ry, cy)), __fmul_rn(rz, cz));
+    v6 = __fadd_rn(v6, det);
+    mx = __fadd_rn(mx, __fmul_rn(det, __fadd_rn(__fadd_rn(rx, ax), bx)));
+    my = __fadd_rn(my, __fmul_rn(det, __fadd_rn(__fadd_rn(ry, ay), by)));
+    mz = __fadd_rn(mz, __fmul_rn(det, __fadd_rn(__fadd_rn(rz, az), bz)));
   };
   edge(R0, B0);
   edge(R1, B1);
@@ -494,10 +512,12 @@ __device__ __noinline__ float4 corner_terms(float4 A4, float4 O, float4 R0, floa
 
 // volume and first moment (frame of v_i) from the summed terms S = (6V, M_x, M_y, M_z)
 // of the corner fan around O; sigma = +-1 (orientation)
-__device__ __noinline__ float4 finish_moments(float sigma, float4 S, float4 O) {
-  float vol = sigma * S.x / 6.f;
-  float s24 = sigma / 24.f;
-  return make_float4(vol, s24 * S.y + vol * O.x, s24 * S.z + vol * O.y, s24 * S.w + vol * O.z);
+__device__ __forceinline__ float4 finish_moments(float sigma, float4 S, float4 O) {
+  float vol = __fdiv_rn(__fmul_rn(sigma, S.x), 6.f);
+  float s24 = __fdiv_rn(sigma, 24.f);
+  return make_float4(vol, __fadd_rn(__fmul_rn(s24, S.y), __fmul_rn(vol, O.x)),
+                     __fadd_rn(__fmul_rn(s24, S.z), __fmul_rn(vol, O.y)),
+                     __fadd_rn(__fmul_rn(s24, S.w), __fmul_rn(vol, O.z)));
 }
 
 // Integrate volume, first moment (frame of v_i) and face areas of the final
@@ -535,7 +555,7 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
       q = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
     } else {
       q = corner(W.pn[pl[0]], W.pm[pl[0]], W.pn[pl[1]], W.pm[pl[1]], W.pn[pl[2]], W.pm[pl[2]]);
-      if (!(q.w <= 3e-3f * sqrtf(q.x * q.x + q.y * q.y + q.z * q.z))) q = refine64(C, a, i, sr[0], sr[1], sr[2]);
+      if (loose(q)) q = refine64(C, a, i, sr[0], sr[1], sr[2]);
     }
     W.tq[t] = q;
     key[r] = corner_key(sr[0], sr[1], sr[2]);

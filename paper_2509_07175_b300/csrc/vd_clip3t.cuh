@@ -444,7 +444,7 @@ __device__ __noinline__ int t_clip(const Dev<float>& C, Poly& P, Masks& Mk, int 
     else { set_error(C.status, VD_ERR_LIMIT); return -1; }
     P.tn[u] = un;
     float4 qc = c3::corner(P.pn[x], P.pm[x], P.pn[y], P.pm[y], Pn, Mn);
-    if (!(qc.w <= 3e-3f * sqrtf(qc.x * qc.x + qc.y * qc.y + qc.z * qc.z)))
+    if (c3::loose(qc))
       qc = c3::refine64(C, a, i, P.psrc[x], P.psrc[y], P.psrc[pl]);
     P.tq[sl] = qc;
     P.twit[sl] = -1;
@@ -502,7 +502,7 @@ __device__ __noinline__ void t_integrate(const Dev<float>& C, Poly& P, const Mas
         q = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
       } else {
         q = c3::corner(P.pn[pl[0]], P.pm[pl[0]], P.pn[pl[1]], P.pm[pl[1]], P.pn[pl[2]], P.pm[pl[2]]);
-        if (!(q.w <= 3e-3f * sqrtf(q.x * q.x + q.y * q.y + q.z * q.z))) q = c3::refine64(C, a, i, sr[0], sr[1], sr[2]);
+        if (c3::loose(q)) q = c3::refine64(C, a, i, sr[0], sr[1], sr[2]);
       }
       P.tq[t] = q;
       unsigned long long kk = c3::corner_key(sr[0], sr[1], sr[2]);
