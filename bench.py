@@ -42,6 +42,10 @@ DESC = {
     "cube2m": "3D clipped VD: unit cube as 6 tets, 2,000,000 uniform sites, FP32",
     "square": "2D clipped VD: unit square as 2 triangles, 1,000 uniform sites, FP64",
     "torus": "restricted VD: torus (500,000 triangles), 200,000 sites, FP32",
+    "box": "3D clipped VD: unit cube as one convex domain (box form), 100,000 uniform sites, FP32",
+    "box5m": "3D clipped VD: unit cube as one convex domain (box form), 5,000,000 uniform sites (white noise), FP32",
+    "grid5m": "3D clipped VD: unit cube as one convex domain (box form), 171^3 = 5,000,211 sites on a "
+              "perturbed grid (+-0.1 h), FP32",
 }
 
 

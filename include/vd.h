@@ -151,6 +151,16 @@ int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype);
 int vd_set_domain(vd_ctx* ctx, const void* verts, int64_t nv, const int32_t* simplices, int64_t m,
                   int simplex_verts);
 
+/* Set the domain to the axis-aligned box [lo, hi] (host pointers, 3 doubles
+ * each, rounded to float) for a 3D FP32 context: the convex-domain form of
+ * Sec. 4.2, where every site's cell starts as the whole box (8 corners, 6 faces)
+ * and is clipped by Alg. 3 -- one piece per site, no tetrahedra and no flood.
+ * Results as for the box split into tetrahedra (measure, centroid, neighbours);
+ * the pieces are (0, i) per site, box faces flagged INT32_MIN.  Clip kernel: one
+ * warp per pair.  VD_ERR_ARG for another dim/dtype or an empty box.
+ * Synchronises the context stream. */
+int vd_set_box(vd_ctx* ctx, const double* lo, const double* hi);
+
 /* Replace the options (NULL restores the defaults). */
 int vd_set_options(vd_ctx* ctx, const vd_options* opt);
 

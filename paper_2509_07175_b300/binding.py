@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "vd_mlp_train": ([P, P, P, I64, I, I, ctypes.c_float, ctypes.c_uint64, P], I),
         "vd_get_candidate_masks": ([P, P], I),
         "vd_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
+        "vd_set_box": ([P, P, P], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -105,7 +106,7 @@ def exported_symbols():
             "vd_update_sites_host", "vd_compute", "vd_copy_result_host", "vd_lloyd", "vd_get_sites",
             "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc",
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
-            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune"]
+            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box"]
 
 
 class _DevArray:
@@ -138,9 +139,10 @@ class Diagram:
     verts: (nv, dim) CUDA tensor of the same dtype; simplices: (m, 3|4) int32.
     """
 
-    def __init__(self, sites, verts, simplices, options: dict | None = None, stream=None):
+    def __init__(self, sites, verts=None, simplices=None, options: dict | None = None, stream=None, box=None):
+        """box = (lo, hi): the axis-aligned box domain (vd_set_box) instead of a mesh."""
         lib = load()
-        if not (sites.is_cuda and verts.is_cuda and simplices.is_cuda):
+        if not sites.is_cuda or (box is None and not (verts.is_cuda and simplices.is_cuda)):
             raise ValueError("inputs must be CUDA tensors")
         self.dtype = sites.dtype
         self.n, self.dim = sites.shape
@@ -155,10 +157,16 @@ class Diagram:
         _check(lib.vd_set_stream(h, ctypes.c_void_p(st.cuda_stream)), "vd_set_stream")
         if options:
             self.set_options(**options)
-        v = verts.to(self.dtype).contiguous()
-        t = simplices.to(torch.int32).contiguous()
-        self.m, self.k = t.shape
-        _check(lib.vd_set_domain(h, v.data_ptr(), v.shape[0], t.data_ptr(), self.m, self.k), "vd_set_domain")
+        if box is not None:
+            lo = (ctypes.c_double * 3)(*[float(x) for x in box[0]])
+            hi = (ctypes.c_double * 3)(*[float(x) for x in box[1]])
+            self.m, self.k = 1, 0
+            _check(lib.vd_set_box(h, lo, hi), "vd_set_box")
+        else:
+            v = verts.to(self.dtype).contiguous()
+            t = simplices.to(torch.int32).contiguous()
+            self.m, self.k = t.shape
+            _check(lib.vd_set_domain(h, v.data_ptr(), v.shape[0], t.data_ptr(), self.m, self.k), "vd_set_domain")
         self.result = None
 
     def set_options(self, **kw):
@@ -318,6 +326,8 @@ def diagram_from_workload(w: dict, device="cuda", options=None):
     dt = torch.float64 if w["f64"] else torch.float32
     dim = 2 if w["mode"] == MODE_2D else 3
     s = torch.tensor(w["sites"][:, :dim], dtype=dt, device=device)
+    if w.get("box") is not None:
+        return Diagram(s, options=options, box=w["box"])
     v = torch.tensor(w["verts"][:, :dim], dtype=dt, device=device)
     t = torch.tensor(w["simp"], dtype=torch.int32, device=device)
     return Diagram(s, v, t, options=options)

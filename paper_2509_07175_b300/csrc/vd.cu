@@ -98,6 +98,8 @@ struct vd_ctx {
   int tuned_mapping = 1, tuned_chunk = 1;
   float tune_ms[8] = {0};         // clip-phase time of each candidate of the last autotune
   bool have_domain = false;
+  bool box = false;               // box domain (vd_set_box)
+  float blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
   long long last_pairs = 0, last_nnz = 0, last_nonempty = 0;
   int last_status = 0;
   int last_where = 0;          // source line of the first device-side error
@@ -199,6 +201,8 @@ static Dev<T> make_dev(vd_ctx* c) {
   D.status = c->status; D.stats = c->stats; D.want_stats = c->opt.stats;
   D.max_clips = c->opt.max_clips; D.max_search = c->opt.max_search; D.max_lambda = c->opt.max_lambda;
   D.wait_ns = (long long)(c->opt.wait_limit_s * 1e9);
+  D.box = c->box ? 1 : 0;
+  for (int d = 0; d < 3; ++d) { D.blo[d] = c->blo[d]; D.bhi[d] = c->bhi[d]; }
   return D;
 }
 
@@ -275,9 +279,19 @@ static void enqueue_compute(vd_ctx* c) {
     c->launches += 2;
   }
   mark(c, 2);
-  k_seed_simplex<T><<<nblk(c->m, 128), 128, 0, s>>>(D);
-  if (MODE != VD_MODE_SURFACE) k_seed_site<T><<<nblk(c->n, 128), 128, 0, s>>>(D, c->L);
-  c->launches += MODE != VD_MODE_SURFACE ? 2 : 1;
+  bool seeded = false;
+  if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) {
+    if (c->box) {
+      k_seed_box<<<nblk(c->n, 256), 256, 0, s>>>(D);
+      c->launches += 1;
+      seeded = true;
+    }
+  }
+  if (!seeded) {
+    k_seed_simplex<T><<<nblk(c->m, 128), 128, 0, s>>>(D);
+    if (MODE != VD_MODE_SURFACE) k_seed_site<T><<<nblk(c->n, 128), 128, 0, s>>>(D, c->L);
+    c->launches += MODE != VD_MODE_SURFACE ? 2 : 1;
+  }
   mark(c, 3);
   bool thread_form = false;
   if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) thread_form = c->cur_mapping == 2;
@@ -354,7 +368,7 @@ static void resolve_mapping(vd_ctx* c) {
     m = c->tuned ? c->tuned_mapping : 1;
     if (ch <= 0) ch = c->tuned ? c->tuned_chunk : 1;
   }
-  if (m == 2 && c->flood_grid_t == 0) m = 1;  // thread per pair: 3D FP32 only
+  if (m == 2 && (c->flood_grid_t == 0 || c->box)) m = 1;  // thread per pair: 3D FP32 tetrahedra only
   c->cur_mapping = m;
   c->cur_chunk = std::max(1, std::min(ch <= 0 ? 1 : ch, 64));
 }
@@ -551,6 +565,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   else return VD_ERR_ARG;
   if (c->dtype == VD_F64 && mode != VD_MODE_2D) return VD_ERR_ARG;  // FP64 path: planar only
   free_domain(c);
+  c->box = false;
   c->mode = mode; c->k = sv; c->nv = nv; c->m = m;
   size_t ts = tsize(c->dtype);
   // host copies for validation and set-up
@@ -788,7 +803,7 @@ static int autotune(vd_ctx* c) {
   int cand_m[8], cand_c[8], nc = 0;
   const int chunks[2] = {1, 4};
   for (int m = 1; m <= 2; ++m) {
-    if (m == 2 && c->flood_grid_t == 0) continue;
+    if (m == 2 && (c->flood_grid_t == 0 || c->box)) continue;
     if (c->opt.chunk > 0) { cand_m[nc] = m; cand_c[nc++] = std::min(c->opt.chunk, 64); continue; }
     for (int k = 0; k < 2; ++k) { cand_m[nc] = m; cand_c[nc++] = chunks[k]; }
   }
@@ -817,6 +832,38 @@ static int autotune(vd_ctx* c) {
   c->tuned = true;
   c->tuned_mapping = cand_m[best];
   c->tuned_chunk = cand_c[best];
+  return VD_OK;
+}
+
+int vd_set_box(vd_ctx* c, const double* lo, const double* hi) {
+  if (!c || !lo || !hi || c->dim != 3 || c->dtype != VD_F32) return VD_ERR_ARG;
+  float l[3], h[3];
+  for (int d = 0; d < 3; ++d) {
+    l[d] = (float)lo[d];
+    h[d] = (float)hi[d];
+    if (!(l[d] < h[d]) || !std::isfinite(l[d]) || !std::isfinite(h[d])) return VD_ERR_ARG;
+  }
+  // the same box as 6 tetrahedra around its main diagonal: sizes the site grid and
+  // the buffers exactly like vd_set_domain (the clip kernel uses the box itself)
+  float v[8][3];
+  for (int k = 0; k < 8; ++k)
+    for (int d = 0; d < 3; ++d) v[k][d] = ((k >> d) & 1) ? h[d] : l[d];
+  const int tets[6][4] = {{0, 1, 3, 7}, {0, 1, 5, 7}, {0, 2, 3, 7}, {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 6, 7}};
+  float* dv = nullptr;
+  int* dt = nullptr;
+  CK(cudaMalloc(&dv, sizeof(v)));
+  cudaError_t e = cudaMalloc(&dt, sizeof(tets));
+  if (e != cudaSuccess) { cudaFree(dv); return VD_ERR_OOM; }
+  int rc = VD_OK;
+  if (cudaMemcpy(dv, v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dt, tets, sizeof(tets), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = VD_ERR_CUDA;
+  if (!rc) rc = vd_set_domain(c, dv, 8, dt, 6, 4);
+  cudaFree(dv);
+  cudaFree(dt);
+  if (rc) return rc;
+  c->box = true;
+  for (int d = 0; d < 3; ++d) { c->blo[d] = l[d]; c->bhi[d] = h[d]; }
   return VD_OK;
 }
 

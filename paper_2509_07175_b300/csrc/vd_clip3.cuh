@@ -38,6 +38,7 @@ struct Warp3 {
   int pref[MAXP];       // reference corner of each face (integration)
   float parea[MAXP][3]; // face vector areas
   unsigned long long pkey[MAXP];  // smallest corner key of each face (integration)
+  unsigned char prank[MAXP];      // rank of each face among the faces by source (integration)
   float4 contrib[MAXT]; // volume / moment terms by corner rank (integration)
   ScanScratch S;
   CornerScratch A;
@@ -71,7 +72,19 @@ __device__ __forceinline__ void face_verts(int f, int& a0, int& a1, int& a2) {
   a2 = f <= 2 ? 3 : 2;
 }
 
+// box face f (axis f/2, lower bound for even f): inside is n.x <= c
+__device__ __forceinline__ void plane_box(const Dev<float>& C, int f, float3 vi, float4& P, float2& M) {
+  int ax = f >> 1;
+  float s = (f & 1) ? 1.f : -1.f;
+  float b = (f & 1) ? C.bhi[ax] : C.blo[ax];
+  float v = ax == 0 ? vi.x : (ax == 1 ? vi.y : vi.z);
+  float c = s * (b - v);
+  P = make_float4(ax == 0 ? s : 0.f, ax == 1 ? s : 0.f, ax == 2 ? s : 0.f, c);
+  M = make_float2(1.f, fabsf(b - v));
+}
+
 __device__ void plane_face(const Dev<float>& C, int a, int f, float3 vi, float4& P, float2& M) {
+  if (C.box) { plane_box(C, f, vi, P, M); return; }
   int l0, l1, l2;
   face_verts(f, l0, l1, l2);
   const int* s = C.simp + 4 * a;
@@ -107,6 +120,16 @@ __device__ __noinline__ ePlane eplane(const Dev<float>& C, int a, int i, int src
     return p;
   }
   int f = -1 - src, l0, l1, l2;
+  if (C.box) {
+    int ax = f >> 1;
+    double sg = (f & 1) ? 1.0 : -1.0;
+    double b = (f & 1) ? (double)C.bhi[ax] : (double)C.blo[ax];
+    ed v = ax == 0 ? vi.x : (ax == 1 ? vi.y : vi.z);
+    p.n = ed3{mk(ax == 0 ? sg : 0.0), mk(ax == 1 ? sg : 0.0), mk(ax == 2 ? sg : 0.0)};
+    ed d = mk(b) - v;
+    p.c = ed{sg * d.v, d.e};
+    return p;
+  }
   face_verts(f, l0, l1, l2);
   const int* s = C.simp + 4 * a;
   const float* A = C.verts + 3 * s[l0];
@@ -471,17 +494,16 @@ __device__ void check_mesh(const Dev<float>& C, Warp3& W, const Masks& Mk, int a
 }
 #endif
 
-// Canonical key of a corner: its three plane sources (bisector site j -> j+4,
-// tet face f -> f), sorted, 21 bits each.  Equal for the same corner whatever
-// sequence of clips produced it (sites beyond 2^21-5 fall back to slot order).
-__device__ __forceinline__ unsigned long long corner_key(int s0, int s1, int s2) {
-  unsigned a = (unsigned)(s0 + 4), b = (unsigned)(s1 + 4), c = (unsigned)(s2 + 4);
-  unsigned t;
+// Canonical key of a corner: the ranks (among the polytope's faces, ordered by
+// source: tet faces first, then bisectors by site) of its three planes, sorted,
+// 6 bits each.  Equal for the same corner whatever sequence of clips produced
+// it, for any number of sites.
+__device__ __forceinline__ unsigned long long corner_key(int r0, int r1, int r2) {
+  unsigned a = (unsigned)r0, b = (unsigned)r1, c = (unsigned)r2, t;
   if (a > b) { t = a; a = b; b = t; }
   if (b > c) { t = b; b = c; c = t; }
   if (a > b) { t = a; a = b; b = t; }
-  return ((unsigned long long)(a & 0x1fffffu) << 42) | ((unsigned long long)(b & 0x1fffffu) << 21) |
-         (unsigned long long)(c & 0x1fffffu);
+  return ((unsigned long long)a << 12) | ((unsigned long long)b << 6) | (unsigned long long)c;
 }
 
 // Volume and first-moment terms of one corner A (its three edge terms, faces in
@@ -532,6 +554,12 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
     W.pref[x] = 0x7fffffff;
     W.pkey[x] = ~0ull;
     W.parea[x][0] = W.parea[x][1] = W.parea[x][2] = 0.f;
+    int rk = 0;
+    if ((Mk.palive >> x) & 1ull) {
+      int sx = W.psrc[x];
+      for (unsigned long long m = Mk.palive; m; m &= m - 1) rk += W.psrc[__ffsll((long long)m) - 1] < sx;
+    }
+    W.prank[x] = (unsigned char)rk;
   }
   __syncwarp();
   unsigned long long key[3];
@@ -549,16 +577,26 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
         if (sr[w] + 4 > sr[w + 1] + 4) { int tt = sr[w]; sr[w] = sr[w + 1]; sr[w + 1] = tt; tt = pl[w]; pl[w] = pl[w + 1]; pl[w + 1] = tt; }
     float4 q;
     if (sr[2] < 0) {
-      int k = 6 - (-1 - sr[0]) - (-1 - sr[1]) - (-1 - sr[2]);  // tet vertex off the three faces
-      const float* V = C.verts + 3 * C.simp[4 * a + k];
-      float qx = V[0] - vi.x, qy = V[1] - vi.y, qz = V[2] - vi.z;
+      float qx, qy, qz;
+      if (C.box) {  // box vertex: one face per axis
+        float b[3];
+        for (int u = 0; u < 3; ++u) {
+          int f = -1 - sr[u];
+          b[f >> 1] = (f & 1) ? C.bhi[f >> 1] : C.blo[f >> 1];
+        }
+        qx = b[0] - vi.x; qy = b[1] - vi.y; qz = b[2] - vi.z;
+      } else {
+        int k = 6 - (-1 - sr[0]) - (-1 - sr[1]) - (-1 - sr[2]);  // tet vertex off the three faces
+        const float* V = C.verts + 3 * C.simp[4 * a + k];
+        qx = V[0] - vi.x; qy = V[1] - vi.y; qz = V[2] - vi.z;
+      }
       q = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
     } else {
       q = corner(W.pn[pl[0]], W.pm[pl[0]], W.pn[pl[1]], W.pm[pl[1]], W.pn[pl[2]], W.pm[pl[2]]);
       if (loose(q)) q = refine64(C, a, i, sr[0], sr[1], sr[2]);
     }
     W.tq[t] = q;
-    key[r] = corner_key(sr[0], sr[1], sr[2]);
+    key[r] = corner_key(W.prank[pl[0]], W.prank[pl[1]], W.prank[pl[2]]);
     atomicMin(&W.pkey[v.x], key[r]); atomicMin(&W.pkey[v.y], key[r]); atomicMin(&W.pkey[v.z], key[r]);
   }
   __syncwarp();
@@ -642,7 +680,40 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
 // other than f = k meet; dual triangles oriented as the boundary of a simplex
 __constant__ unsigned char TET_TV[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
 
+// the dual mesh of the box: corner k = (x, y, z sides in bits 0, 1, 2) where one
+// face of each axis meets, oriented by the parity of k; across the dual edge
+// between two faces lies the corner that differs on the third axis
+__device__ void init_box(const Dev<float>& C, Warp3& W, Masks& Mk, float3 vi, int lane) {
+  if (lane < 6) {
+    float4 P;
+    float2 M;
+    plane_box(C, lane, vi, P, M);
+    W.pn[lane] = P; W.pm[lane] = M; W.psrc[lane] = -1 - lane;
+  }
+  if (lane < 8) {
+    int k = lane, sx = k & 1, sy = (k >> 1) & 1, sz = (k >> 2) & 1;
+    float qx = (sx ? C.bhi[0] : C.blo[0]) - vi.x, qy = (sy ? C.bhi[1] : C.blo[1]) - vi.y,
+          qz = (sz ? C.bhi[2] : C.blo[2]) - vi.z;
+    W.tq[k] = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
+    unsigned char fx = (unsigned char)sx, fy = (unsigned char)(2 + sy), fz = (unsigned char)(4 + sz);
+    if (((sx + sy + sz) & 1) == 0) {
+      W.tv[k] = make_uchar4(fx, fy, fz, 0);
+      W.tn[k] = make_uchar4((unsigned char)(k ^ 4), (unsigned char)(k ^ 1), (unsigned char)(k ^ 2), 0);
+    } else {
+      W.tv[k] = make_uchar4(fx, fz, fy, 0);
+      W.tn[k] = make_uchar4((unsigned char)(k ^ 2), (unsigned char)(k ^ 1), (unsigned char)(k ^ 4), 0);
+    }
+    W.twit[k] = -1;
+  }
+  Mk.alive[0] = 0xFFu; Mk.alive[1] = Mk.alive[2] = 0;
+  Mk.in[0] = Mk.in[1] = Mk.in[2] = 0;
+  Mk.out[0] = Mk.out[1] = Mk.out[2] = 0;
+  Mk.palive = 0x3Full;
+  __syncwarp();
+}
+
 __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, float3 vi, int lane) {
+  if (C.box) { init_box(C, W, Mk, vi, lane); return; }
   if (lane < 4) {
     float4 P;
     float2 M;
@@ -685,8 +756,8 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   init_tet(C, W, Mk, a, i, vi, lane);
   // orientation of the dual mesh against space: with the corner table below, the
   // edge-term sum of integrate() has the sign of the tet's orientation
-  float sigma;
-  {
+  float sigma = 1.f;  // the box's dual mesh is oriented like a positive tet
+  if (!C.box) {
     const int* sp = C.simp + 4 * a;
     const float *P0 = C.verts + 3 * sp[0], *P1 = C.verts + 3 * sp[1], *P2 = C.verts + 3 * sp[2],
                 *P3 = C.verts + 3 * sp[3];
@@ -776,7 +847,9 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
         int src = W.psrc[x];
         if (src >= 0) {
           myflag[h] = src;
-          push_pair(C, a, src);
+          if (!C.box) push_pair(C, a, src);  // the box form seeds every site itself
+        } else if (C.box) {
+          myflag[h] = FLAG_BOUNDARY;
         } else {
           int b = C.adj[4 * a + (-1 - src)];
           myflag[h] = b >= 0 ? -(b + 1) : FLAG_BOUNDARY;

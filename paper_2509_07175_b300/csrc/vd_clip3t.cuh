@@ -473,8 +473,16 @@ __device__ __noinline__ int t_clip(const Dev<float>& C, Poly& P, Masks& Mk, int 
 __device__ __noinline__ void t_integrate(const Dev<float>& C, Poly& P, const Masks& Mk, int a, int i, float3 vi,
                                          float sigma, float& vol, float3& m1, unsigned long long& posarea) {
   unsigned long long pkey[MAXP];
-  unsigned char pref[MAXP];
-  for (int x = 0; x < MAXP; ++x) pkey[x] = ~0ull;
+  unsigned char pref[MAXP], prank[MAXP];
+  for (int x = 0; x < MAXP; ++x) {
+    pkey[x] = ~0ull;
+    int rk = 0;
+    if ((Mk.palive >> x) & 1ull) {
+      int sx = P.psrc[x];
+      for (unsigned long long m = Mk.palive; m; m &= m - 1) rk += P.psrc[__ffsll((long long)m) - 1] < sx;
+    }
+    prank[x] = (unsigned char)rk;
+  }
   unsigned long long key[MAXT];
   unsigned char list[MAXT];
   int nalive = 0;
@@ -505,7 +513,7 @@ __device__ __noinline__ void t_integrate(const Dev<float>& C, Poly& P, const Mas
         if (c3::loose(q)) q = c3::refine64(C, a, i, sr[0], sr[1], sr[2]);
       }
       P.tq[t] = q;
-      unsigned long long kk = c3::corner_key(sr[0], sr[1], sr[2]);
+      unsigned long long kk = c3::corner_key(prank[pl[0]], prank[pl[1]], prank[pl[2]]);
       key[t] = kk;
       int vx = b0(v), vy = b1(v), vz = b2(v);
       if (kk < pkey[vx]) pkey[vx] = kk;

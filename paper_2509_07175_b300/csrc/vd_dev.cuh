@@ -45,6 +45,11 @@ struct Dev {
   int want_stats;
   int max_clips, max_search, max_lambda;
   long long wait_ns;
+  // box domain (Sec. 4.2, a convex domain with few corners): one piece per site,
+  // the box [blo, bhi] clipped by the site's bisectors; faces 0..5 = -x, +x, -y,
+  // +y, -z, +z
+  int box;
+  float blo[3], bhi[3];
 };
 
 __device__ __forceinline__ unsigned long long pair_key(int a, int i) {

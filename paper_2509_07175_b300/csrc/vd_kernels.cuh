@@ -132,6 +132,14 @@ __global__ void k_seed_simplex(const __grid_constant__ Dev<T> C) {
   if (i >= 0 && i < C.n) push_pair(C, a, i);
 }
 
+// box domain: every site's cell is one piece, (0, i); no pair set is needed
+__global__ void k_seed_box(Dev<float> C) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  C.queue[i] = pair_key(0, i);
+  if (i == 0) atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)C.n);
+}
+
 struct Locator {
   const int* start;   // [B+1]
   const int* items;   // simplex ids

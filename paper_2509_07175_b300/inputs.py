@@ -223,6 +223,16 @@ def uniform_sites(n: int, dim: int, seed: int, lo: float = 0.0, hi: float = 1.0,
     return _dedupe(gen(n), gen)
 
 
+def perturbed_grid_sites(k: int, seed: int, amp: float = 0.1):
+    """Centres of a k^3 lattice in the unit cube moved by U[-amp h, amp h] per
+    coordinate (h = 1/k), rounded to float32."""
+    rng = _rng(seed)
+    h = 1.0 / k
+    g = (np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), -1).reshape(-1, 3) + 0.5) * h
+    g = g + rng.uniform(-amp * h, amp * h, size=g.shape)
+    return g.astype(np.float32).astype(np.float64)
+
+
 def lattice_sites(N: int, dim: int, lo: float = 0.0, hi: float = 1.0):
     """Sites at the centres of an N^dim lattice of boxes: lo + (k+1/2) h."""
     h = (hi - lo) / N
@@ -319,6 +329,24 @@ def workload(name: str, n: int | None = None, seed: int | None = None):
         seed = (SEED_BASE + {"cube": 2, "cube1m": 6, "cube2m": 5}[name]) if seed is None else seed
         sites = uniform_sites(n, 3, seed)
         return dict(name=name, mode=MODE_3D, sites=sites, verts=verts, simp=simp, f64=False)
+    if name in ("box", "box5m"):
+        # the unit cube as one convex domain (the box form); the same cube as 6
+        # tetrahedra is what the oracle clips
+        verts, simp = cube_6tet()
+        n = {"box": 100_000, "box5m": 5_000_000}[name] if n is None else n
+        seed = (SEED_BASE + {"box": 2, "box5m": 7}[name]) if seed is None else seed
+        sites = uniform_sites(n, 3, seed)
+        return dict(name=name, mode=MODE_3D, sites=sites, verts=verts, simp=simp, f64=False,
+                    box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)))
+    if name == "grid5m":
+        # perturbed grid: the centres of a 171^3 lattice (5,000,211 sites) moved by
+        # U[-0.1 h, 0.1 h] per coordinate, in the unit cube as one convex domain
+        verts, simp = cube_6tet()
+        k = 171 if n is None else max(2, int(round(n ** (1.0 / 3.0))))
+        seed = SEED_BASE + 8 if seed is None else seed
+        sites = perturbed_grid_sites(k, seed)
+        return dict(name=name, mode=MODE_3D, sites=sites, verts=verts, simp=simp, f64=False,
+                    box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)))
     if name == "shell":
         verts, simp = shell_domain()
         n = 1_000_000 if n is None else n

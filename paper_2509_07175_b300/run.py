@@ -22,7 +22,8 @@ from . import inputs as I
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", default="cube", choices=["square", "cube", "cube1m", "cube2m", "shell", "torus"])
+    ap.add_argument("--workload", default="cube",
+                    choices=["square", "cube", "cube1m", "cube2m", "shell", "torus", "box", "box5m", "grid5m"])
     ap.add_argument("--n", type=int, default=None, help="sites (default: the workload's own)")
     ap.add_argument("--form", default="learned", choices=["plain", "learned"])
     ap.add_argument("--proposal", default="distance", choices=["distance", "mlp"])

@@ -1,0 +1,119 @@
+"""The box form (Sec. 4.2: a convex domain with few corners, every site's cell
+clipped from the whole box; one piece per site) against the oracle, which clips
+the same cube split into 6 tetrahedra and sums the pieces of each site."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2509_07175_b300 import binding as B
+from paper_2509_07175_b300 import inputs as I
+from vdcheck import CENT_RTOL, MEAS_RTOL, gpu_csr
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("measure", "centroid", "nbr_off", "nbr_idx")
+
+
+def _per_site_check(w, r, ids=None):
+    n = len(w["sites"])
+    ids = np.arange(n) if ids is None else np.asarray(ids)
+    op = O.Oracle(4, w["sites"], w["verts"], w["simp"])
+    pieces = op.site_pieces(ids) if len(ids) < n else op.enumerate()
+    om, oc, onb = O.per_site(n, w["sites"], pieces, site_ids=ids)
+    gm = r["measure"].double().cpu().numpy()[ids]
+    gc = r["centroid"].double().cpu().numpy()[ids]
+    gnb = gpu_csr(r)
+    assert ((om > 0) == (gm > 0)).all()
+    rel = np.abs(gm - om) / np.maximum(om, 1e-300)
+    assert rel.max() <= MEAS_RTOL, rel.max()
+    dc = np.linalg.norm(gc - oc, axis=1)
+    assert (dc <= CENT_RTOL * np.linalg.norm(oc, axis=1)).all()
+    for k, i in enumerate(ids):
+        assert gnb[i] == onb[k], (i, gnb[i], onb[k])
+    return float(rel.max())
+
+
+@pytest.mark.parametrize("n", [1, 2, 37, 3000])
+def test_box_against_oracle(gpu, n):
+    w = I.workload("box", n, seed=I.SEED_BASE + 0x150 + n)
+    d = B.diagram_from_workload(w, options=dict(stats=1))
+    r = d.compute()
+    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
+    assert r["stats"]["pairs"] == n
+    _per_site_check(w, r)
+    if n == 1:
+        assert abs(float(r["measure"][0]) - 1.0) < 1e-6
+        assert np.allclose(r["centroid"][0].cpu().numpy(), 0.5, atol=1e-6)
+    assert abs(float(r["measure"].double().sum()) - 1.0) < 1e-5
+    d.close()
+
+
+def test_box_lattice_closed_form(gpu):
+    # sites at the centres of an 8^3 lattice: every cell is its lattice box
+    N = 8
+    s = I.lattice_sites(N, 3)
+    w = dict(name="box", mode=4, sites=s, verts=I.cube_6tet()[0], simp=I.cube_6tet()[1], f64=False,
+             box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)))
+    d = B.diagram_from_workload(w)
+    r = d.compute()
+    assert r["status"] == 0
+    m = r["measure"].double().cpu().numpy()
+    assert np.allclose(m, N ** -3, rtol=1e-5, atol=0)
+    assert np.allclose(r["centroid"].double().cpu().numpy(), s, atol=1e-6)
+    nb = gpu_csr(r)
+    idx = {tuple(np.round(p * N - 0.5).astype(int)): k for k, p in enumerate(s)}
+    for k, p in enumerate(s):
+        c = np.round(p * N - 0.5).astype(int)
+        want = sorted(idx[tuple(c + e)] for e in np.vstack([np.eye(3, dtype=int), -np.eye(3, dtype=int)])
+                      if tuple(c + e) in idx)
+        assert nb[k] == want, k
+    d.close()
+
+
+def test_box_100k_sampled_and_forms(gpu):
+    """100,000 uniform sites (the cube workload's sites) in the box form: sampled
+    oracle parity; the learned form (distance ranking and network) is
+    bit-identical to the plain box form; neighbour sets equal those of the
+    6-tetrahedra form and measures agree within the tolerance."""
+    w = I.workload("box")
+    d = B.diagram_from_workload(w, options=dict(stats=1))
+    plain = d.compute()
+    rng = np.random.default_rng(31)
+    _per_site_check(w, plain, np.sort(rng.choice(len(w["sites"]), 200, replace=False)))
+    d.set_options(learned=1, topk=24, stats=1)
+    _res = d.compute()
+    for k in KEYS:
+        assert torch.equal(plain[k], _res[k]), k
+    d.mlp_init(3)
+    d.set_options(learned=1, topk=16, proposal=B.PROPOSAL_MLP)
+    _res = d.compute()
+    for k in KEYS:
+        assert torch.equal(plain[k], _res[k]), k
+    tets = B.diagram_from_workload(I.workload("cube")).compute()
+    assert torch.equal(plain["nbr_off"], tets["nbr_off"]) and torch.equal(plain["nbr_idx"], tets["nbr_idx"])
+    rel = (plain["measure"].double() - tets["measure"].double()).abs() / tets["measure"].double()
+    assert float(rel.max()) < 2e-5
+    d.close()
+
+
+def test_perturbed_grid_small(gpu):
+    w = I.workload("grid5m", 20 ** 3)
+    d = B.diagram_from_workload(w)
+    r = d.compute()
+    assert r["status"] == 0
+    rng = np.random.default_rng(33)
+    _per_site_check(w, r, np.sort(rng.choice(len(w["sites"]), 300, replace=False)))
+    d.close()
+
+
+def test_box_lloyd_graph(gpu):
+    w = I.workload("box", 20000, seed=I.SEED_BASE + 0x160)
+    a, b = B.diagram_from_workload(w), B.diagram_from_workload(w)
+    a.lloyd(5, use_graph=True)
+    b.lloyd(5, use_graph=False)
+    sa = a.sites()
+    assert torch.equal(sa, b.sites())
+    assert float(sa.min()) >= 0.0 and float(sa.max()) <= 1.0
+    a.close()
+    b.close()
