@@ -142,6 +142,19 @@ typedef struct {
  * dtype not in {VD_F32, VD_F64}. */
 int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype);
 
+/* Power diagram in the plane (the paper's extension to power diagrams by
+ * lifting): the power distance of x to site i is |x - v_i|^2 - w_i.  Creates a
+ * 3D FP32 context whose sites are the lifted points (x_i, y_i, sqrt(eta - w_i)),
+ * eta = max_i w_i (found on the device): for x in the plane z = 0,
+ * |x - p_i|^2 = |x - v_i|^2 - w_i + eta, so the restricted diagram of the lifted
+ * sites on a planar triangle mesh at z = 0 (vd_set_domain with 3 vertices per
+ * simplex) is the power diagram on that mesh.  xy: device float [n*2]; w: device
+ * float [n]; copied.  The power weights the diagram realises are exactly
+ * -h_i^2 + eta with h_i the float lift, i.e. w_i up to the rounding of h_i.  Cells
+ * may be empty (dominated sites): measure 0, centroid = the lifted site.
+ * VD_ERR_ARG for a weight that is not finite. */
+int vd_create_power2d(vd_ctx** out, const float* xy, const float* w, int64_t n);
+
 /* Set the domain M = {T_a} (Sec. 2.1).  verts: device pointer, nv*dim elements of
  * the context dtype; simplices: device pointer, m*simplex_verts int32 vertex
  * indices (3: triangles, 4: tetrahedra).  Copied and validated (indices in

@@ -8,7 +8,9 @@ follows: Eq. 1 for the cell, Sec. 2.2 for the face flags).
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` (brute force, lattice closed form, n=1 and n=2
-closed forms, partition invariants, neighbour symmetry).
+closed forms, partition invariants, neighbour symmetry; power weights: equal
+weights reduce to the Voronoi diagram, the two-site weighted closed form,
+brute force against the generalised security radius, a planted sign flip).
 """
 from __future__ import annotations
 
@@ -63,6 +65,8 @@ def _load():
         lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64, P,
                                    ctypes.c_int, ctypes.c_int]
         lib.orc_destroy.argtypes = [P]
+        lib.orc_set_weights.argtypes = [P, P]
+        lib.orc_set_weights.restype = None
         lib.orc_adjacency.argtypes = [P, P]
         lib.orc_adjacency.restype = ctypes.c_int64
         for f in (lib.orc_pieces, lib.orc_enumerate, lib.orc_site_pieces):
@@ -122,7 +126,7 @@ class Oracle:
     4 (tetrahedra).  ``brute``: clip by all n-1 bisectors (tiny inputs only).
     """
 
-    def __init__(self, mode, sites, verts, simp, brute=False, nthreads=None):
+    def __init__(self, mode, sites, verts, simp, brute=False, nthreads=None, weights=None):
         self.mode = int(mode)
         self.sites = np.ascontiguousarray(sites, dtype=np.float64).reshape(-1, 3)
         self.verts = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, 3)
@@ -134,6 +138,11 @@ class Oracle:
         lib = _load()
         self._h = lib.orc_create(self.mode, len(self.sites), _ptr(self.sites), len(self.verts), _ptr(self.verts),
                                  len(self.simp), _ptr(self.simp), int(bool(brute)), int(nt))
+        if weights is not None:
+            # power diagram: |x - v_i|^2 - w_i <= |x - v_j|^2 - w_j
+            self.weights = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+            assert len(self.weights) == len(self.sites)
+            lib.orc_set_weights(self._h, _ptr(self.weights))
 
     def close(self):
         if getattr(self, "_h", None):

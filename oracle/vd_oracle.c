@@ -117,6 +117,8 @@ typedef struct {
   kdtree kd_sites;
   kdtree kd_cent;    /* simplex centroids */
   double* cent;      /* m*3 */
+  double* w;         /* n power weights (power diagram), or NULL (Voronoi diagram) */
+  double wmax;       /* largest weight */
 } orc_ctx;
 
 /* ------------------------------------------------------------------------- */
@@ -276,7 +278,10 @@ typedef struct {
     if (p->kind == PL_BIS) {                                                          \
       const double* vj = C->sites + 3 * (int64_t)p->a;                               \
       for (int d = 0; d < 3; ++d) n[d] = S##_sub(S##_c(vj[d]), S##_c(vi[d]));         \
-      *c = S##_scale(S##_dot3(n, n), 0.5);                                            \
+      if (C->w)  /* power bisector: |x-v_i|^2 - w_i <= |x-v_j|^2 - w_j */              \
+        *c = S##_scale(S##_sub(S##_dot3(n, n), S##_sub(S##_c(C->w[p->a]), S##_c(C->w[site]))), 0.5); \
+      else                                                                            \
+        *c = S##_scale(S##_dot3(n, n), 0.5);                                          \
       return;                                                                         \
     }                                                                                 \
     const double* A = C->verts + 3 * (int64_t)p->a;                                  \
@@ -773,7 +778,12 @@ static void compute_piece(workspace* w, int64_t a, int64_t i, piece_out* o) {
       int64_t got = kd_knn(&C->kd_sites, vi, k, i, w->knn_id, w->knn_d);
       for (int64_t t = done_upto; t < got; ++t) {
         double R = piece_radius(w);
-        if (sqrt(w->knn_d[t]) > 2.0 * R * (1.0 + 1e-9)) { finished = 1; break; }
+        /* a bisector at distance |v_j - v_i| = D lies at (D^2 - (w_j - w_i)) / (2D) >=
+           (D^2 - dw) / (2D) from v_i, dw = wmax - w_i: it cannot cut the piece (inside
+           the ball of radius R) once D >= R + sqrt(R^2 + dw); dw = 0 gives D >= 2R */
+        double dw = C->w ? C->wmax - C->w[i] : 0.0;
+        if (dw < 0) dw = 0;
+        if (sqrt(w->knn_d[t]) > (R + sqrt(R * R + dw)) * (1.0 + 1e-9)) { finished = 1; break; }
         rc = clip_by_site(w, w->knn_id[t]);
         if (rc != 0) { finished = 1; break; }
       }
@@ -865,8 +875,20 @@ orc_ctx* orc_create(int mode, int64_t n, const double* sites, int64_t nv, const 
   return C;
 }
 
+/* power weights for the sites (NULL: back to the Voronoi diagram); copied */
+void orc_set_weights(orc_ctx* C, const double* w) {
+  free(C->w);
+  C->w = NULL;
+  if (!w) return;
+  C->w = (double*)malloc(sizeof(double) * (C->n ? C->n : 1));
+  memcpy(C->w, w, sizeof(double) * C->n);
+  C->wmax = -INFINITY;
+  for (int64_t i = 0; i < C->n; ++i) if (C->w[i] > C->wmax) C->wmax = C->w[i];
+}
+
 void orc_destroy(orc_ctx* C) {
   if (!C) return;
+  free(C->w);
   kd_free(&C->kd_sites); kd_free(&C->kd_cent);
   free(C->sites); free(C->verts); free(C->simp); free(C->adj); free(C->cent); free(C);
 }
@@ -943,6 +965,14 @@ static void item_simplex(job* J, workspace* w, int64_t a) {
     int64_t id; double dd;
     kd_knn(&C->kd_sites, c, 1, -1, &id, &dd);
     double R = (sqrt(dd) + 2 * rho) * (1 + 1e-9) + 1e-12;
+    if (C->w) {
+      /* power diagram: |x - v_i|^2 <= (d_NN(c) + rho)^2 + (w_max - w_min) for x of T_a
+         owned by v_i, so |c - v_i| <= rho + sqrt((d_NN + rho)^2 + dw) */
+      double wmin = INFINITY;
+      for (int64_t u = 0; u < C->n; ++u) if (C->w[u] < wmin) wmin = C->w[u];
+      double dn = sqrt(dd) + rho;
+      R = (rho + sqrt(dn * dn + (C->wmax - wmin))) * (1 + 1e-9) + 1e-12;
+    }
     kd_range_rec(&C->kd_sites, c, R * R, 0, C->kd_sites.n, 0, &cand);
     /* deterministic order */
     for (int64_t u = 1; u < cand.n; ++u)

@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "vd_get_candidate_masks": ([P, P], I),
         "vd_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
         "vd_set_box": ([P, P, P], I),
+        "vd_create_power2d": ([ctypes.POINTER(P), P, P, I64], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -106,7 +107,8 @@ def exported_symbols():
             "vd_update_sites_host", "vd_compute", "vd_copy_result_host", "vd_lloyd", "vd_get_sites",
             "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc",
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
-            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box"]
+            "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box",
+            "vd_create_power2d"]
 
 
 class _DevArray:
@@ -139,18 +141,31 @@ class Diagram:
     verts: (nv, dim) CUDA tensor of the same dtype; simplices: (m, 3|4) int32.
     """
 
-    def __init__(self, sites, verts=None, simplices=None, options: dict | None = None, stream=None, box=None):
-        """box = (lo, hi): the axis-aligned box domain (vd_set_box) instead of a mesh."""
+    def __init__(self, sites, verts=None, simplices=None, options: dict | None = None, stream=None, box=None,
+                 weights=None):
+        """box = (lo, hi): the axis-aligned box domain (vd_set_box) instead of a mesh.
+        weights (n,) with planar sites (n, 2) and a planar triangle mesh: the power
+        diagram (vd_create_power2d; the mesh is placed at z = 0)."""
         lib = load()
         if not sites.is_cuda or (box is None and not (verts.is_cuda and simplices.is_cuda)):
             raise ValueError("inputs must be CUDA tensors")
-        self.dtype = sites.dtype
-        self.n, self.dim = sites.shape
         self._keep = []
         h = ctypes.c_void_p()
-        s = sites.contiguous()
-        _check(lib.vd_create(ctypes.byref(h), s.data_ptr(), self.n, self.dim,
-                             VD_F64 if self.dtype == torch.float64 else VD_F32), "vd_create")
+        if weights is not None:
+            xy = sites.to(torch.float32).contiguous()
+            wt = weights.to(device=sites.device, dtype=torch.float32).contiguous()
+            _check(lib.vd_create_power2d(ctypes.byref(h), xy.data_ptr(), wt.data_ptr(), xy.shape[0]),
+                   "vd_create_power2d")
+            self.dtype = torch.float32
+            self.n, self.dim = xy.shape[0], 3
+            verts = torch.cat([verts.to(torch.float32), torch.zeros((verts.shape[0], 1), dtype=torch.float32,
+                                                                    device=verts.device)], 1)
+        else:
+            self.dtype = sites.dtype
+            self.n, self.dim = sites.shape
+            s = sites.contiguous()
+            _check(lib.vd_create(ctypes.byref(h), s.data_ptr(), self.n, self.dim,
+                                 VD_F64 if self.dtype == torch.float64 else VD_F32), "vd_create")
         self._h = h
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st

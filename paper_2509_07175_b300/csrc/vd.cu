@@ -517,6 +517,32 @@ int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype) {
   return VD_OK;
 }
 
+int vd_create_power2d(vd_ctx** out, const float* xy, const float* w, int64_t n) {
+  if (!out || !xy || !w || n < 1 || n > (int64_t)0x3fffffff) return VD_ERR_ARG;
+  *out = nullptr;
+  float* lifted = nullptr;
+  int* scratch = nullptr;  // [0] ordered max weight, [1] bad-weight flag
+  if (cudaMalloc(&lifted, sizeof(float) * 3 * n) != cudaSuccess) return VD_ERR_OOM;
+  if (cudaMalloc(&scratch, 2 * sizeof(int)) != cudaSuccess) { cudaFree(lifted); return VD_ERR_OOM; }
+  int init[2] = {(int)0x80000000, 0};
+  int host[2] = {0, 0};
+  int rc = VD_OK;
+  if (cudaMemcpy(scratch, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) rc = VD_ERR_CUDA;
+  if (!rc) {
+    k_power_max<<<std::max(1u, std::min(nblk(n, 256), 1024u)), 256>>>(w, n, scratch);
+    k_power_lift<<<nblk(n, 256), 256>>>(xy, w, n, scratch, lifted, scratch + 1);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(host, scratch, sizeof(host), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = VD_ERR_CUDA;
+    else if (host[1])
+      rc = VD_ERR_ARG;  // a weight that is not finite
+  }
+  if (!rc) rc = vd_create(out, lifted, n, 3, VD_F32);
+  cudaFree(lifted);
+  cudaFree(scratch);
+  return rc;
+}
+
 int vd_update_sites(vd_ctx* c, const void* sites) {
   if (!c || !sites) return VD_ERR_ARG;
   c->sites_fresh = c->knn_fresh = false;

@@ -132,6 +132,34 @@ __global__ void k_seed_simplex(const __grid_constant__ Dev<T> C) {
   if (i >= 0 && i < C.n) push_pair(C, a, i);
 }
 
+// ---------------------------------------------------------------------------
+// power diagrams in the plane by lifting: p_i = (x_i, y_i, sqrt(eta - w_i)) with
+// eta = max w, so |x - p_i|^2 = |x - v_i|^2 - w_i + eta for x in the plane z = 0
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ordered_bits(float f) {
+  int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7fffffff;  // monotone in f as a signed integer
+}
+__device__ __forceinline__ float from_ordered(int b) { return __int_as_float(b >= 0 ? b : b ^ 0x7fffffff); }
+
+__global__ void k_power_max(const float* w, long long n, int* best) {
+  int m = ordered_bits(-3.0e38f);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    m = max(m, ordered_bits(w[t]));
+  m = __reduce_max_sync(FULL, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(best, m);
+}
+
+__global__ void k_power_lift(const float* xy, const float* w, long long n, const int* best, float* out, int* bad) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  float eta = from_ordered(*best), wt = w[t];
+  if (!(wt <= eta) || !isfinite(wt)) { atomicExch(bad, 1); wt = eta; }
+  out[3 * t] = xy[2 * t];
+  out[3 * t + 1] = xy[2 * t + 1];
+  out[3 * t + 2] = sqrtf(eta - wt);
+}
+
 // box domain: every site's cell is one piece, (0, i); no pair set is needed
 __global__ void k_seed_box(Dev<float> C) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;

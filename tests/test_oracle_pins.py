@@ -235,3 +235,94 @@ def test_planted_mistake_is_caught():
             assert np.abs(meas - np.array(g["measure"])).max() > 1e-3
         finally:
             O._lib = saved
+
+
+# ----- power diagrams (power distance |x - v_i|^2 - w_i) ---------------------------
+
+def _power_case(mode, n, seed):
+    v, s = _domain(mode)
+    dim = 2 if mode == 2 else 3
+    sites = I.uniform_sites(n, dim, seed, f32=False)
+    measure = I.domain_measure(mode, v, s)
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(-measure / n, measure / n, n)  # the paper's weight range
+    return v, s, sites, w
+
+
+@pytest.mark.parametrize("mode,n", [(2, 120), (4, 60)])
+def test_power_equal_weights_is_voronoi(mode, n):
+    # equal weights cancel in every power bisector: the power diagram is the Voronoi diagram
+    v, s, sites, _ = _power_case(mode, n, 21)
+    pv = O.Oracle(mode, sites, v, s).enumerate()
+    pw = O.Oracle(mode, sites, v, s, weights=np.full(n, 0.37)).enumerate()
+    _compare(pv, pw, tol=1e-12)
+
+
+def _two_site_power(mode, dw, oracle_mod=O):
+    # two sites on a line parallel to an axis, 0.5 apart, weights 0 and dw: the power
+    # bisector is the plane x* = (x2^2 - x1^2 - dw) / (2 (x2 - x1)) = 0.5 - dw
+    v, s = _domain(mode)
+    sites = np.array([[0.25, 0.5, 0.0], [0.75, 0.5, 0.0]]) if mode == 2 else \
+        np.array([[0.5, 0.5, 0.25], [0.5, 0.5, 0.75]])
+    p = oracle_mod.Oracle(mode, sites, v, s, brute=True, weights=np.array([0.0, dw])).enumerate()
+    meas, cen, nb = oracle_mod.per_site(2, sites, p)
+    return meas, cen, nb
+
+
+@pytest.mark.parametrize("mode", [2, 4])
+@pytest.mark.parametrize("dw", [0.0, 0.1, -0.2, 0.3, 0.8])
+def test_power_two_sites_closed_form(mode, dw):
+    meas, cen, nb = _two_site_power(mode, dw)
+    xs = 0.5 - dw
+    if xs <= 0:  # site 0 is dominated everywhere: empty cell
+        assert meas[0] == 0 and nb[0] == [] and abs(meas[1] - 1.0) < 1e-12
+        return
+    assert abs(meas[0] - xs) < 1e-12 and abs(meas[1] - (1 - xs)) < 1e-12
+    ax = 0 if mode == 2 else 2
+    assert abs(cen[0][ax] - xs / 2) < 1e-12 and abs(cen[1][ax] - (1 + xs) / 2) < 1e-12
+    assert nb[0] == [1] and nb[1] == [0]
+
+
+@pytest.mark.parametrize("mode,n,seed", [(2, 150, 31), (4, 80, 32), (2, 60, 33)])
+def test_power_brute_equals_security_radius(mode, n, seed):
+    v, s, sites, w = _power_case(mode, n, seed)
+    pb = O.Oracle(mode, sites, v, s, brute=True, weights=w).enumerate()
+    ps = O.Oracle(mode, sites, v, s, brute=False, weights=w).enumerate()
+    _compare(pb, ps)
+    # the cells still partition the domain
+    total = I.domain_measure(mode, v, s)
+    assert abs(pb.meas.sum() - total) < 1e-12 * max(1.0, total) * 10
+
+
+def test_power_planted_sign_flip_is_caught():
+    """The weight difference with the wrong sign in the power bisector must break the
+    two-site closed form (planted in a copy of the oracle source, compiled on the CPU)."""
+    import ctypes
+    import subprocess
+    import tempfile
+    src = open(os.path.join(os.path.dirname(O.__file__), "vd_oracle.c")).read()
+    bad = src.replace("S##_sub(S##_c(C->w[p->a]), S##_c(C->w[site]))", "S##_sub(S##_c(C->w[site]), S##_c(C->w[p->a]))")
+    assert bad != src
+    with tempfile.TemporaryDirectory() as d:
+        cpath, lpath = os.path.join(d, "bad.c"), os.path.join(d, "libbad.so")
+        open(cpath, "w").write(bad)
+        subprocess.check_call(["gcc", "-O1", "-shared", "-fPIC", "-o", lpath, cpath, "-lpthread", "-lm"])
+        saved = O._lib
+        try:
+            O._lib = None
+            lib = ctypes.CDLL(lpath)
+            P = ctypes.c_void_p
+            lib.orc_create.restype = P
+            lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64, P,
+                                       ctypes.c_int, ctypes.c_int]
+            lib.orc_set_weights.argtypes = [P, P]
+            lib.orc_set_weights.restype = None
+            lib.orc_enumerate.restype = ctypes.POINTER(O._Result)
+            lib.orc_enumerate.argtypes = [P]
+            lib.orc_free_result.argtypes = [ctypes.POINTER(O._Result)]
+            lib.orc_destroy.argtypes = [P]
+            O._lib = lib
+            meas, _, _ = _two_site_power(2, 0.1)
+            assert abs(meas[0] - 0.4) > 1e-3
+        finally:
+            O._lib = saved
