@@ -48,6 +48,7 @@ struct vd_ctx {
   int* simp = nullptr;
   int* adj = nullptr;
   signed char* fsgn = nullptr;
+  signed char* tsgn = nullptr;    // [m] 3D: orientation sign of each tetrahedron
   int* loc_start = nullptr;
   int* loc_items = nullptr;
   Locator L{};
@@ -177,6 +178,7 @@ static Dev<T> make_dev(vd_ctx* c) {
   std::memset(&D, 0, sizeof(D));
   D.mode = c->mode; D.n = (int)c->n; D.m = (int)c->m; D.k = c->k;
   D.sites = (const T*)c->sites; D.verts = (const T*)c->verts; D.simp = c->simp; D.adj = c->adj; D.fsgn = c->fsgn;
+  D.tsgn = c->tsgn;
   D.delta = (const T*)c->delta;
   D.G.gx = c->gx; D.G.gy = c->gy; D.G.gz = c->gz;
   D.G.ox = (T)c->ox; D.G.oy = (T)c->oy; D.G.oz = (T)c->oz;
@@ -613,7 +615,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   for (long long v = 0; v < nv; ++v)
     for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], hv[3 * v + d]); hi[d] = std::max(hi[d], hv[3 * v + d]); }
   double measure = 0;
-  std::vector<signed char> fs((size_t)(m * sv), 1);
+  std::vector<signed char> fs((size_t)(m * sv), 1), orient((size_t)m, 1);
   for (long long a = 0; a < m; ++a) {
     const double* P[4];
     for (int l = 0; l < sv; ++l) P[l] = &hv[3 * (size_t)hs[(size_t)(a * sv + l)]];
@@ -623,6 +625,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
       double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) + u[2] * (v[0] * w[1] - v[1] * w[0]);
       if (!(std::fabs(det) > 0)) return VD_ERR_DOMAIN;
       measure += std::fabs(det) / 6.0;
+      orient[(size_t)a] = det > 0 ? 1 : -1;
       for (int f = 0; f < 4; ++f) {
         int l0 = f == 0 ? 1 : 0, l1 = f <= 1 ? 2 : 1, l2 = f <= 2 ? 3 : 2;
         double e1[3], e2[3], dd[3];
@@ -657,6 +660,8 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   CK(cudaMemcpy(c->simp, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->adj, hadj.data(), hadj.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->fsgn, fs.data(), fs.size(), cudaMemcpyHostToDevice));
+  DALLOC(c->tsgn, signed char, m, true);
+  CK(cudaMemcpy(c->tsgn, orient.data(), orient.size(), cudaMemcpyHostToDevice));
   // simplex locator: bins over the mesh box, each listing the simplices whose box meets it
   if (mode != VD_MODE_SURFACE) {
     int dims = mode == VD_MODE_2D ? 2 : 3;

@@ -620,14 +620,7 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
   t_init_tet(C, P, Mk, a, vi);
   float sigma;
   {
-    const int* sp = C.simp + 4 * a;
-    const float *P0 = C.verts + 3 * sp[0], *P1 = C.verts + 3 * sp[1], *P2 = C.verts + 3 * sp[2],
-                *P3 = C.verts + 3 * sp[3];
-    double ux = (double)P1[0] - P0[0], uy = (double)P1[1] - P0[1], uz = (double)P1[2] - P0[2];
-    double vx = (double)P2[0] - P0[0], vy = (double)P2[1] - P0[1], vz = (double)P2[2] - P0[2];
-    double wx = (double)P3[0] - P0[0], wy = (double)P3[1] - P0[1], wz = (double)P3[2] - P0[2];
-    double det = ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx);
-    sigma = det > 0 ? 1.f : -1.f;
+    sigma = (float)C.tsgn[a];
   }
   bool empty = false;
   int nclip = 0;

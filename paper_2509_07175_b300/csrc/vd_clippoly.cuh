@@ -202,7 +202,7 @@ __device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const Nbr
   T px = vi[0] + sx, py = vi[1] + sy, pz = vi[2] + sz;
   if (L.r32 > 0.f) {
     T s = sqrt(sx * sx + sy * sy + sz * sz);
-    if ((double)(T(2) * s) * (1.0 + 1e-5) + 4e-7 * (double)(fabs(px) + fabs(py) + fabs(pz)) <= (double)L.r32) {
+    if ((float)(T(2) * s) * (1.f + 2e-5f) + 4e-7f * (float)(fabs(px) + fabs(py) + fabs(pz)) <= L.r32) {
       T d2 = T(1e30);
       int kk = 0x7fffffff;
       if (L.id >= 0) {

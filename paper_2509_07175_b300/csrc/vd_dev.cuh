@@ -18,6 +18,7 @@ struct Dev {
   const int* simp;       // [m*k]
   const int* adj;        // [m*k] neighbour across the face opposite local vertex f, -1: boundary
   const signed char* fsgn;  // [m*k] +-1: orientation making the face normal point outward
+  const signed char* tsgn;  // [m] 3D: +-1, the sign of the tetrahedron's orientation determinant
   const T* delta;        // [n] half the distance to the nearest other site (Sec. 5.1)
   GridView<T> G;
   // learned proposal: candidate bisector neighbours of each site (ranked)
@@ -230,7 +231,8 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
   // learned form: when the ball of radius |q - v_i| around q lies inside the ball
   // holding v_i's 32 nearest sites (2 |q - v_i| <= r32), every site that could be
   // closer to q than v_i is in the list, which settles the test exactly
-  if (L.r32 > 0.f && (double)L.r32 >= 2.0 * ((double)di + (double)delta) * (1.0 + 1e-5) + 1e-30) {
+  // (float arithmetic: its rounding, below 1e-6 relative, is inside the 2e-5 margin)
+  if (L.r32 > 0.f && L.r32 >= 2.f * (float)(di + delta) * (1.f + 2e-5f)) {
     *listed += 1;
     T ld = T(1e30), lo = T(1e30);
     int lk = 0x7fffffff, lok = 0x7fffffff;
