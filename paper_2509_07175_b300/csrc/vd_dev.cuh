@@ -244,10 +244,16 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
       if (f < -B) { ld = d2; lk = k; }
       else if (f <= B && exact(k) < 0) { lo = d2; lok = k; }
     }
-    warp_argmin(ld, lk);
-    if (lk != 0x7fffffff) { *wit = lk; return 1; }
-    warp_argmin(lo, lok);
-    if (lok != 0x7fffffff) { *wit = lok; return 1; }
+    if (__any_sync(FULL, lk != 0x7fffffff)) {
+      warp_argmin(ld, lk);
+      *wit = lk;
+      return 1;
+    }
+    if (__any_sync(FULL, lok != 0x7fffffff)) {
+      warp_argmin(lo, lok);
+      *wit = lok;
+      return 1;
+    }
     *wit = -1;
     return 0;
   }
