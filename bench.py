@@ -49,6 +49,30 @@ DESC = {
 }
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_flood launch,
+# from a single-pass ncu capture of the learned form (top 24) on the full workload,
+# valid only for the kernel sources it was taken on (their hash)
+FLOOD_TRAFFIC = {"source_hash": "182ad42de5e763a1",
+                 "bytes": {"shell": 10.70e9 + 2.73e9, "cube": 38.1e6 + 75.0e6}}
+
+
+def _source_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2509_07175_b300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def flood_traffic(workload):
+    """Captured bytes per launch, or None when the kernel changed since the capture."""
+    if _source_hash() != FLOOD_TRAFFIC["source_hash"]:
+        return None
+    return FLOOD_TRAFFIC["bytes"].get(workload)
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -353,7 +377,11 @@ def main():
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "peak_source": f"{sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "flops_per_launch": flops, "clip_ms": clip_s * 1e3,
-                     "clip_share": (clip_s * 1e3) / (total_ms / args.steps), "traffic": None},
+                     "clip_share": (clip_s * 1e3) / (total_ms / args.steps),
+                     "traffic": flood_traffic(args.workload),
+                     "traffic_note": "dram bytes per k_flood launch, single-pass ncu capture of the same kernel "
+                                     "(learned form, distance ranking, top 24); null once the kernel sources "
+                                     "differ from the captured ones"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "autotune": {"choice": ("warp" if tune["mapping"] == 1 else "thread") + f" per pair, chunk {tune['chunk']}",
