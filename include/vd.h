@@ -47,7 +47,9 @@ enum {
                              simplex, face shared by more than two simplices) */
   VD_ERR_UNCERTAIN = -7,  /* reserved: a sign could not be certified even in FP64
                              (reported through the stats, results still written) */
-  VD_ERR_STATE = -8       /* call out of order (e.g. vd_compute before vd_set_domain) */
+  VD_ERR_STATE = -8,      /* call out of order (e.g. vd_compute before vd_set_domain) */
+  VD_ERR_DUPLICATE = -9   /* two sites coincide: their bisector is undefined and Eq. 1 would
+                             give both the same cell (found by vd_compute's nearest-site pass) */
 };
 
 enum { VD_F32 = 0, VD_F64 = 1 };

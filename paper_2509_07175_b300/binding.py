@@ -24,7 +24,8 @@ STAT_NAMES = ("pairs", "nonempty", "nn_queries", "corner_tests", "clips", "lambd
 PHASE_NAMES = ("grid", "delta", "seed", "clip", "reduce")
 
 ERRORS = {0: "ok", -1: "VD_ERR_ARG", -2: "VD_ERR_CUDA", -3: "VD_ERR_OOM", -4: "VD_ERR_CAPACITY",
-          -5: "VD_ERR_LIMIT", -6: "VD_ERR_DOMAIN", -7: "VD_ERR_UNCERTAIN", -8: "VD_ERR_STATE"}
+          -5: "VD_ERR_LIMIT", -6: "VD_ERR_DOMAIN", -7: "VD_ERR_UNCERTAIN", -8: "VD_ERR_STATE",
+          -9: "VD_ERR_DUPLICATE"}
 
 
 class VDError(RuntimeError):

@@ -485,6 +485,7 @@ const char* vd_strerror(int code) {
     case VD_ERR_DOMAIN: return "invalid domain mesh";
     case VD_ERR_UNCERTAIN: return "sign not certified in FP64";
     case VD_ERR_STATE: return "call out of order";
+    case VD_ERR_DUPLICATE: return "two sites coincide";
     default: return "unknown error";
   }
 }

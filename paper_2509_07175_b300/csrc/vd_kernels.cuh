@@ -112,6 +112,7 @@ __global__ void k_delta(const __grid_constant__ Dev<T> C, T* delta) {
   if (i >= C.n) return;
   T d2;
   int k = thread_nearest(C.G, C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], i, d2);
+  if (k >= 0 && k < C.n && d2 == T(0)) set_error(C.status, VD_ERR_DUPLICATE);  // coincident sites
   delta[i] = (k >= 0 && k < C.n) ? T(0.5) * sqrt(d2) : T(1);
 }
 

@@ -34,6 +34,11 @@ def test_strerror_without_gpu():
     lib = binding.load()
     assert lib.vd_strerror(-4) == b"capacity exceeded (polytope, queue, pair set or flag buffer)"
     assert lib.vd_strerror(0) == b"ok"
+    assert lib.vd_strerror(-9) == b"two sites coincide"
+    # every error code of the header has a name
+    src = open(os.path.join(ROOT, "include", "vd.h")).read()
+    for code in re.findall(r"VD_ERR_[A-Z]+ = (-\d+)", src):
+        assert lib.vd_strerror(int(code)) != b"unknown error", code
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu():

@@ -117,3 +117,21 @@ def test_box_lloyd_graph(gpu):
     assert float(sa.min()) >= 0.0 and float(sa.max()) <= 1.0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name", ["box5m", "grid5m"])
+def test_box_5m_sampled(gpu, name):
+    """The 5M-site box workloads at full size: oracle on a sample of sites, the
+    cells partition the box, learned form bit-identical to plain."""
+    w = I.workload(name)
+    d = B.diagram_from_workload(w, options=dict(stats=1))
+    r = d.compute()
+    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
+    assert abs(float(r["measure"].double().sum()) - 1.0) < 1e-5
+    rng = np.random.default_rng(43)
+    _per_site_check(w, r, np.sort(rng.choice(len(w["sites"]), 120, replace=False)))
+    d.set_options(learned=1, topk=24)
+    lr = d.compute()
+    for k in KEYS:
+        assert torch.equal(r[k], lr[k]), k
+    d.close()

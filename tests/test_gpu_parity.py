@@ -160,3 +160,49 @@ def test_learned_form_equals_plain_bitwise(gpu, name, n):
         for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
             assert torch.equal(plain[key], lr[key]), (k, key)
     d.close()
+
+
+@pytest.mark.parametrize("mode", [2, 4])
+def test_coincident_sites_are_reported(gpu, mode):
+    """Two equal sites have no bisector and Eq. 1 would give both the same cell:
+    the compute reports VD_ERR_DUPLICATE instead of a double cover."""
+    from paper_2509_07175_b300 import binding as B
+    if mode == 2:
+        v, s = I.square_grid_tris(2)
+        sites = I.uniform_sites(200, 2, I.SEED_BASE + 0x170, f32=False)
+        f64 = True
+    else:
+        v, s = I.cube_6tet()
+        sites = I.uniform_sites(500, 3, I.SEED_BASE + 0x171)
+        f64 = False
+    sites[7] = sites[123]
+    w = _w(mode, sites, v, s, f64=f64)
+    d = B.diagram_from_workload(w)
+    with pytest.raises(B.VDError) as e:
+        d.compute()
+    assert e.value.code == -9
+    sites[7, 0] = np.nextafter(np.float32(sites[7, 0]), np.float32(2)) if not f64 else np.nextafter(sites[7, 0], 2)
+    d.update_sites(torch.tensor(sites[:, :2 if mode == 2 else 3], dtype=torch.float64 if f64 else torch.float32,
+                                device="cuda"))
+    r = d.compute()   # one ulp apart: a valid, if thin, pair of cells
+    assert r["status"] == 0
+    d.close()
+
+
+def test_cube2m_sampled(gpu):
+    """Config 5 at full size: 2,000,000 uniform sites in the 6-tet cube; oracle on
+    a sample of sites, learned form (network ranking) bit-identical to plain."""
+    from paper_2509_07175_b300 import binding as B
+    w = I.workload("cube2m")
+    d, r, p = gpu_run(w)
+    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
+    rng = np.random.default_rng(41)
+    pick = np.sort(rng.choice(len(w["sites"]), 150, replace=False))
+    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
+    compare_full(w, r, p, op, sites_subset=pick)
+    d.mlp_init(9)
+    d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=24)
+    lr = d.compute()
+    for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+        assert torch.equal(r[key], lr[key]), key
+    d.close()
