@@ -176,42 +176,52 @@ struct Locator {
   double ox, oy, oz, ih;
 };
 
-__device__ __forceinline__ double orient3(const double* a, const double* b, const double* c, const double* p) {
-  double ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
-  double vx = c[0] - a[0], vy = c[1] - a[1], vz = c[2] - a[2];
-  double wx = p[0] - a[0], wy = p[1] - a[1], wz = p[2] - a[2];
+template <typename R>
+__device__ __forceinline__ R orient3(const R* a, const R* b, const R* c, const R* p) {
+  R ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
+  R vx = c[0] - a[0], vy = c[1] - a[1], vz = c[2] - a[2];
+  R wx = p[0] - a[0], wy = p[1] - a[1], wz = p[2] - a[2];
   return ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx);
 }
-__device__ __forceinline__ double orient2(const double* a, const double* b, const double* p) {
+template <typename R>
+__device__ __forceinline__ R orient2(const R* a, const R* b, const R* p) {
   return (b[0] - a[0]) * (p[1] - a[1]) - (b[1] - a[1]) * (p[0] - a[0]);
 }
 
+// The simplex containing each site seeds (simplex, site).  Any simplex that meets
+// the site's cell is a valid seed (the output does not depend on the seeds), so
+// the barycentric test runs in the context's precision with a tolerance of 1e-5
+// of the simplex for FP32: a site within that of a face may seed either side.
 template <typename T>
 __global__ void k_seed_site(const __grid_constant__ Dev<T> C, Locator L) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C.n) return;
-  double p[3] = {(double)C.sites[3 * i], (double)C.sites[3 * i + 1], (double)C.sites[3 * i + 2]};
-  int bx = (int)floor((p[0] - L.ox) * L.ih), by = (int)floor((p[1] - L.oy) * L.ih), bz = (int)floor((p[2] - L.oz) * L.ih);
+  T p[3] = {C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]};
+  int bx = (int)floor(((double)p[0] - L.ox) * L.ih), by = (int)floor(((double)p[1] - L.oy) * L.ih),
+      bz = (int)floor(((double)p[2] - L.oz) * L.ih);
   if (bx < 0 || by < 0 || bz < 0 || bx >= L.bx || by >= L.by || bz >= L.bz) return;
+  const T tol = sizeof(T) == 4 ? T(1e-5) : T(0);
   int b = (bz * L.by + by) * L.bx + bx;
   for (int t = L.start[b]; t < L.start[b + 1]; ++t) {
     int a = L.items[t];
-    double V[4][3];
+    T V[4][3];
     for (int l = 0; l < C.k; ++l)
-      for (int d = 0; d < 3; ++d) V[l][d] = (double)C.verts[3 * C.simp[C.k * a + l] + d];
+      for (int d = 0; d < 3; ++d) V[l][d] = C.verts[3 * C.simp[C.k * a + l] + d];
     bool in;
     // barycentric signs: p substituted for each vertex keeps the orientation
     if (C.k == 4) {
-      double o = orient3(V[0], V[1], V[2], V[3]);
-      double s0 = orient3(p, V[1], V[2], V[3]), s1 = orient3(V[0], p, V[2], V[3]);
-      double s2 = orient3(V[0], V[1], p, V[3]), s3 = orient3(V[0], V[1], V[2], p);
+      T o = orient3(V[0], V[1], V[2], V[3]);
+      T s0 = orient3(p, V[1], V[2], V[3]), s1 = orient3(V[0], p, V[2], V[3]);
+      T s2 = orient3(V[0], V[1], p, V[3]), s3 = orient3(V[0], V[1], V[2], p);
+      T lim = -tol * fabs(o);
       if (o < 0) { s0 = -s0; s1 = -s1; s2 = -s2; s3 = -s3; }
-      in = s0 >= 0 && s1 >= 0 && s2 >= 0 && s3 >= 0;
+      in = s0 >= lim && s1 >= lim && s2 >= lim && s3 >= lim;
     } else {
-      double o = orient2(V[0], V[1], V[2]);
-      double s0 = orient2(p, V[1], V[2]), s1 = orient2(V[0], p, V[2]), s2 = orient2(V[0], V[1], p);
+      T o = orient2(V[0], V[1], V[2]);
+      T s0 = orient2(p, V[1], V[2]), s1 = orient2(V[0], p, V[2]), s2 = orient2(V[0], V[1], p);
+      T lim = -tol * fabs(o);
       if (o < 0) { s0 = -s0; s1 = -s1; s2 = -s2; }
-      in = s0 >= 0 && s1 >= 0 && s2 >= 0;
+      in = s0 >= lim && s1 >= lim && s2 >= lim;
     }
     if (in) { push_pair(C, a, i); return; }
   }
