@@ -349,7 +349,9 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     int t = r * 32 + lane;
-    bool o = bit(Mk.alive, t) && side_of(C, W, a, i, t, pl) < 0;
+    // a corner already proven inside Omega_i lies inside every bisector half-space
+    // of v_i (Omega_i is their intersection): no side test (Sec. 3.3)
+    bool o = bit(Mk.alive, t) && !bit(Mk.in, t) && side_of(C, W, a, i, t, pl) < 0;
     om[r] = __ballot_sync(FULL, o);
     R[r] = 0;
   }

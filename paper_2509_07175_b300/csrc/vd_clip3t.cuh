@@ -366,7 +366,7 @@ search:
 __device__ __noinline__ int t_clip(const Dev<float>& C, Poly& P, Masks& Mk, int a, int i, int pl, int p) {
   unsigned om[3] = {0, 0, 0}, R[3] = {0, 0, 0};
   for (int r = 0; r < 3; ++r) {
-    unsigned m = Mk.alive[r];
+    unsigned m = Mk.alive[r] & ~Mk.in[r];  // corners proven inside Omega_i stay (Sec. 3.3)
     while (m) {
       int b = __ffs(m) - 1;
       m &= m - 1;

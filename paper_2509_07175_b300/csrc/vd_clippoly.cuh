@@ -291,7 +291,8 @@ search:
 // returns 0 clipped, 1 empty, -1 error.  nv is updated.
 template <typename T>
 __device__ __noinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int pl, int p, int& nv, int lane) {
-  bool o = lane < nv && side_of(C, W, a, i, lane, nv, pl) < 0;
+  // a corner already proven inside Omega_i stays (inside every bisector half-space of v_i)
+  bool o = lane < nv && W.vst[lane] != 1 && side_of(C, W, a, i, lane, nv, pl) < 0;
   unsigned om = __ballot_sync(FULL, o);
   if (!((om >> p) & 1u)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
   int s = p, e = p, run = 1;
