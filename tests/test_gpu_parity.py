@@ -20,13 +20,13 @@ def _w(mode, sites, verts, simp, f64=False, name="case"):
     return dict(name=name, mode=mode, sites=sites, verts=verts, simp=simp, f64=f64)
 
 
-def _full_check(w, brute=False, options=None):
+def _full_check(w, brute=False, options=None, meas_floor=0.0):
     d, r, p = gpu_run(w, options=options)
     assert r["status"] == 0
     assert r["stats"]["uncertain"] == 0
     op = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], brute=brute).enumerate()
     assert op.stats["uncertain"] == 0
-    err = compare_full(w, r, p, op)
+    err = compare_full(w, r, p, op, meas_floor=meas_floor)
     # pieces partition each simplex
     per = np.zeros(len(w["simp"]))
     pm = p["measure"].double().cpu().numpy()
@@ -205,4 +205,31 @@ def test_cube2m_sampled(gpu):
     lr = d.compute()
     for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
         assert torch.equal(r[key], lr[key]), key
+    d.close()
+
+
+@pytest.mark.parametrize("mode,n,seed", [(4, 3000, 51), (2, 1500, 52), (3, 1200, 53)])
+def test_sites_outside_the_domain(gpu, mode, n, seed):
+    """Sites spread over twice the domain's extent: many have no simplex of their
+    own (no site seed), some cells are empty, others reach into the domain from
+    outside; the pieces must still match the oracle."""
+    if mode == 4:
+        v, s = I.cube_6tet()
+        sites = I.uniform_sites(n, 3, I.SEED_BASE + seed, lo=-0.5, hi=1.5)
+    elif mode == 2:
+        v, s = I.square_grid_tris(4)
+        sites = I.uniform_sites(n, 2, I.SEED_BASE + seed, lo=-0.5, hi=1.5)
+    else:
+        v, s = I.small_torus()
+        sites = I.uniform_sites(n, 3, I.SEED_BASE + seed, lo=-1.6, hi=1.6)
+    w = _w(mode, sites, v, s)
+    # cells reaching in from outside can be slivers far from their site: measures
+    # are checked relative to max(m, mean cell measure), the mean taken over the
+    # sites inside the domain's bounding box
+    lo, hi = v.min(axis=0), v.max(axis=0)
+    dim = 2 if mode == 2 else 3
+    inside = np.all((sites[:, :dim] >= lo[:dim]) & (sites[:, :dim] <= hi[:dim]), axis=1).sum()
+    _full_check(w, meas_floor=I.domain_measure(mode, v, s) / max(1, int(inside)))
+    d, r, _ = gpu_run(w)
+    assert (r["measure"] == 0).any()   # some cells miss the domain entirely
     d.close()
