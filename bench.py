@@ -49,11 +49,12 @@ DESC = {
 }
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_flood launch,
-# from a single-pass ncu capture of the learned form (top 24) on the full workload,
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the 3D
+# clip kernel, from a single-pass ncu capture of the learned form (top 24, split) on
+# the full workload,
 # valid only for the kernel sources it was taken on (their hash)
-FLOOD_TRAFFIC = {"source_hash": "6aa439e696282ff3",
-                 "bytes": {"shell": 10.72e9 + 2.74e9, "cube": 38.2e6 + 75.0e6}}
+FLOOD_TRAFFIC = {"source_hash": "5e6dedccdd0c4f19",
+                 "bytes": {"shell": 7.04e9 + 1.21e9}}
 
 
 def _source_hash():
@@ -212,6 +213,8 @@ def main():
     ap.add_argument("--topk", type=int, default=24)
     ap.add_argument("--proposal", default="mlp", choices=["mlp", "distance"],
                     help="ranking of the 32 nearest sites in the learned form")
+    ap.add_argument("--split", default="on", choices=["on", "off"],
+                    help="3D tetrahedra: interior sites' cells whole after the boundary pass (Alg. 5)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -244,7 +247,8 @@ def main():
     if mlp:
         L.load_state(d, training["state"])
     prop = B.PROPOSAL_MLP if mlp else B.PROPOSAL_DISTANCE
-    form = dict(learned=0 if args.plain else 1, topk=args.topk, proposal=prop)
+    split = int(args.split == "on" and w["mode"] == B.MODE_3D and w.get("box") is None)
+    form = dict(learned=0 if args.plain else 1, topk=args.topk, proposal=prop, split=split)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
@@ -270,12 +274,12 @@ def main():
     # distance ranking beside the headline form: identical output, timed the same way
     beside = {}
     if not args.plain:
-        d.set_options(learned=0)
+        d.set_options(learned=0, split=split)
         ref = d.compute()
         nb = max(1, min(5, args.steps))
-        beside["plain"] = time_form(dict(learned=0), nb)
+        beside["plain"] = time_form(dict(learned=0, split=split), nb)
         if mlp:
-            beside["learned_distance"] = time_form(dict(learned=1, topk=args.topk,
+            beside["learned_distance"] = time_form(dict(learned=1, topk=args.topk, split=split,
                                                         proposal=B.PROPOSAL_DISTANCE), nb)
     # counters for the roofline numerator (an untimed run with the counters on)
     d.set_options(stats=1, **form)
@@ -371,17 +375,19 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w["f64"] else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": DESC[args.workload], "n_sites": n,
                    "n_simplices": len(w["simp"]), "pairs": counts["pairs"], "nonempty_pieces": counts["nonempty"],
+                   "split": ({"whole_cells": counts["whole_cells"], "boundary_sites": counts["boundary_sites"]}
+                             if split else None),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_flood (Alg. 3 clip + flood)", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "k_flood<float, 3D> (Alg. 3 clip + flood)", "bound": "alu", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "peak_source": f"{sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "flops_per_launch": flops, "clip_ms": clip_s * 1e3,
                      "clip_share": (clip_s * 1e3) / (total_ms / args.steps),
                      "traffic": flood_traffic(args.workload),
-                     "traffic_note": "dram bytes per k_flood launch, single-pass ncu capture of the same kernel "
-                                     "(learned form, distance ranking, top 24); null once the kernel sources "
-                                     "differ from the captured ones"},
+                     "traffic_note": "dram bytes per launch of the 3D clip kernel, single-pass ncu capture of "
+                                     "the same kernel (learned form, distance ranking, top 24, split as timed); "
+                                     "null once the kernel sources differ from the captured ones"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "autotune": {"choice": ("warp" if tune["mapping"] == 1 else "thread") + f" per pair, chunk {tune['chunk']}",
@@ -392,7 +398,7 @@ def main():
                                          "list_tests")},
         "form": ("plain (Sec. 3.2 / 5.1 search)" if args.plain else
                  f"learned+batched ({args.proposal} ranking of the 32 nearest, top-{args.topk}; "
-                 "output bit-identical to plain)"),
+                 "output bit-identical to plain)") + ("; Alg. 5 split (interior cells whole)" if split else ""),
     }
     step_med = statistics.median(step_ms)
     for name, ms in beside.items():

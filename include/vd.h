@@ -79,6 +79,8 @@ enum {
   VD_STAT_ERROR_LINE = 15,    /* source line of the first device-side error (diagnostics) */
   VD_STAT_DIAG = 16,          /* 16..23: first FP64 decision that was not certified or was an
                                  exact tie: simplex, site, the 4 plane sources, tie flag, kind */
+  VD_STAT_WHOLE_CELLS = 24,   /* split = 1: sites whose cell was computed whole (always) */
+  VD_STAT_BOUNDARY_SITES = 25,/* split = 1: sites whose cell meets the boundary surface (always) */
   VD_STAT_LIST_TESTS = 30,    /* point-in-cell tests and queries settled from the 32 nearest
                                  sites of the cell's site, with no grid scan (learned form) */
   VD_STAT_MAPPING = 31,       /* clip-kernel mapping used: mapping | chunk << 8 (always) */
@@ -108,6 +110,17 @@ typedef struct {
   int proposal;            /* learned form's ranking of the 32 nearest sites: VD_PROPOSAL_DISTANCE
                               (the topk nearest) or VD_PROPOSAL_MLP (the topk largest logits of
                               the context's network, vd_mlp_*) */
+  int split;               /* 3D tetrahedra (FP32), Alg. 5: 1 first computes the restricted
+                              diagram on the domain's boundary triangles; a site whose
+                              restricted cell there is empty and that lies strictly inside a
+                              tetrahedron has its whole Voronoi cell inside the domain and gets
+                              one piece, (m, i): the mesh's bounding box clipped by its
+                              bisectors (Sec. 4.2).  The pieces of the other sites are the
+                              per-tetrahedron pieces, reached from the boundary pieces' incident
+                              tetrahedra (and the site's own) through negative flags.  Measures,
+                              centroids and neighbours are those of split = 0 (the same cells,
+                              summed in fewer pieces); ignored in other modes and by vd_set_box.
+                              Clip kernel: one warp per pair. */
 } vd_options;
 
 enum { VD_PROPOSAL_DISTANCE = 0, VD_PROPOSAL_MLP = 1 };

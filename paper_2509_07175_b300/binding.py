@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("stats", ctypes.c_int), ("queue_capacity", ctypes.c_int64), ("max_clips", ctypes.c_int),
                 ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
                 ("timing", ctypes.c_int), ("grid_density", ctypes.c_double), ("topk", ctypes.c_int),
-                ("proposal", ctypes.c_int)]
+                ("proposal", ctypes.c_int), ("split", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -223,7 +223,8 @@ class Diagram:
             "n_pieces": int(r.n_pieces),
             "stats": dict(zip(STAT_NAMES, [int(x) for x in r.stats][:len(STAT_NAMES)]),
                           error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]],
-                          list_tests=int(r.stats[30]), mapping=int(r.stats[31]) & 255,
+                          list_tests=int(r.stats[30]), whole_cells=int(r.stats[24]),
+                          boundary_sites=int(r.stats[25]), mapping=int(r.stats[31]) & 255,
                           chunk=int(r.stats[31]) >> 8),
             "phase_ms": dict(zip(PHASE_NAMES, [float(x) for x in r.phase_ms][:len(PHASE_NAMES)])),
         }

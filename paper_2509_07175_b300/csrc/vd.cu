@@ -101,6 +101,15 @@ struct vd_ctx {
   bool have_domain = false;
   bool box = false;               // box domain (vd_set_box)
   float blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+  // split (Alg. 5, 3D tetrahedra FP32): the boundary triangles of the mesh, the
+  // tetrahedron each belongs to, their edge adjacency, the mesh's bounding box
+  bool split_ok = false;
+  long long mb = 0;
+  int *bsimp = nullptr, *badj = nullptr, *btet = nullptr;
+  int* bnd = nullptr;             // [n] 1: boundary site (set by the boundary pass)
+  float mlo[3] = {0, 0, 0}, mhi[3] = {0, 0, 0};
+  int flood_grid_s = 0;           // boundary pass: surface form of the clip kernel
+  size_t flood_smem_s = 0;
   long long last_pairs = 0, last_nnz = 0, last_nonempty = 0;
   int last_status = 0;
   int last_where = 0;          // source line of the first device-side error
@@ -164,6 +173,8 @@ static void free_domain(vd_ctx* c) {
   for (void* p : c->dom_allocs) cudaFree(p);
   c->dom_allocs.clear();
   c->have_domain = false;
+  c->split_ok = false;
+  c->bsimp = c->badj = c->btet = c->bnd = nullptr;
   c->computed = false;
   c->sites_fresh = c->knn_fresh = false;
   c->tuned = false;
@@ -172,6 +183,10 @@ static void free_domain(vd_ctx* c) {
 // ---------------------------------------------------------------------------
 // device context view
 // ---------------------------------------------------------------------------
+static bool split_active(const vd_ctx* c) {
+  return c->opt.split && c->split_ok && !c->box && c->mode == VD_MODE_3D && c->dtype == VD_F32;
+}
+
 template <typename T>
 static Dev<T> make_dev(vd_ctx* c) {
   Dev<T> D;
@@ -205,6 +220,9 @@ static Dev<T> make_dev(vd_ctx* c) {
   D.wait_ns = (long long)(c->opt.wait_limit_s * 1e9);
   D.box = c->box ? 1 : 0;
   for (int d = 0; d < 3; ++d) { D.blo[d] = c->blo[d]; D.bhi[d] = c->bhi[d]; }
+  D.split = split_active(c) ? 1 : 0;
+  if (D.split)
+    for (int d = 0; d < 3; ++d) { D.blo[d] = c->mlo[d]; D.bhi[d] = c->mhi[d]; }
   return D;
 }
 
@@ -287,6 +305,25 @@ static void enqueue_compute(vd_ctx* c) {
       k_seed_box<<<nblk(c->n, 256), 256, 0, s>>>(D);
       c->launches += 1;
       seeded = true;
+    } else if (D.split) {
+      // Alg. 5: the restricted diagram on the boundary triangles (surface form of
+      // the clip kernel on the same pair set, counters off), then the 3D seeds
+      Dev<float> S = D;
+      S.mode = VD_MODE_SURFACE; S.m = (int)c->mb; S.k = 3; S.simp = c->bsimp; S.adj = c->badj;
+      S.fsgn = nullptr; S.tsgn = nullptr; S.want_stats = 0; S.split = 0; S.box = 0;
+      unsigned pg = (unsigned)std::max(1, c->nsm * 8);
+      unsigned long long* seeds = (unsigned long long*)c->pm1;  // free until the 3D flood writes it
+      cudaMemsetAsync(c->bnd, 0, sizeof(int) * c->n, s);
+      k_seed_simplex<float><<<nblk(c->mb, 128), 128, 0, s>>>(S);
+      k_flood<float, VD_MODE_SURFACE><<<c->flood_grid_s, FLOOD_WARPS * 32, c->flood_smem_s, s>>>(S, 1);
+      k_split_mark<<<pg, 256, 0, s>>>(S, c->btet, c->bnd, seeds);
+      cudaMemsetAsync(c->hash, 0xFF, sizeof(unsigned long long) * (c->hmask + 1), s);
+      cudaMemsetAsync(c->queue, 0xFF, sizeof(unsigned long long) * c->qcap, s);
+      cudaMemsetAsync(c->ctr, 0, sizeof(unsigned long long) * CTR_SEEDS, s);  // keeps the seed count
+      k_split_push<<<pg, 256, 0, s>>>(D, seeds);
+      k_split_site<<<nblk(c->n, 128), 128, 0, s>>>(D, c->L, c->bnd);
+      c->launches += 5;
+      seeded = true;
     }
   }
   if (!seeded) {
@@ -354,10 +391,20 @@ static int flood_config(vd_ctx* c) {
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood<T, MODE>, FLOOD_WARPS * 32, c->flood_smem));
   c->flood_grid = std::max(1, per_sm) * c->nsm;
   c->flood_grid_t = 0;
+  c->flood_grid_s = 0;
   if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) {
     int per_sm_t = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_flood_thread, FLOOD_T_THREADS, 0));
     c->flood_grid_t = std::max(1, per_sm_t) * c->nsm;
+    // the split's boundary pass runs the surface form
+    using WS = typename WarpOf<float, VD_MODE_SURFACE>::type;
+    c->flood_smem_s = sizeof(WS) * FLOOD_WARPS;
+    CK(cudaFuncSetAttribute(k_flood<float, VD_MODE_SURFACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->flood_smem_s));
+    int per_sm_s = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_flood<float, VD_MODE_SURFACE>, FLOOD_WARPS * 32,
+                                                     c->flood_smem_s));
+    c->flood_grid_s = std::max(1, per_sm_s) * c->nsm;
   }
   return VD_OK;
 }
@@ -370,7 +417,7 @@ static void resolve_mapping(vd_ctx* c) {
     m = c->tuned ? c->tuned_mapping : 1;
     if (ch <= 0) ch = c->tuned ? c->tuned_chunk : 1;
   }
-  if (m == 2 && (c->flood_grid_t == 0 || c->box)) m = 1;  // thread per pair: 3D FP32 tetrahedra only
+  if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c))) m = 1;  // thread per pair: 3D FP32 tetrahedra only
   c->cur_mapping = m;
   c->cur_chunk = std::max(1, std::min(ch <= 0 ? 1 : ch, 64));
 }
@@ -444,7 +491,8 @@ struct FaceKey {
 
 }  // namespace
 
-static int build_adjacency(int k, long long m, const std::vector<int>& simp, std::vector<int>& adj) {
+static int build_adjacency(int k, long long m, const std::vector<int>& simp, std::vector<int>& adj,
+                           bool strict = true) {
   std::vector<FaceKey> F((size_t)(m * k));
   for (long long a = 0; a < m; ++a)
     for (int f = 0; f < k; ++f) {
@@ -462,7 +510,7 @@ static int build_adjacency(int k, long long m, const std::vector<int>& simp, std
   for (size_t t = 0; t < F.size();) {
     size_t u = t + 1;
     while (u < F.size() && F[t].same(F[u])) ++u;
-    if (u - t > 2) return VD_ERR_DOMAIN;
+    if (u - t > 2 && strict) return VD_ERR_DOMAIN;
     if (u - t == 2) {
       adj[(size_t)(F[t].s * k + F[t].f)] = (int)F[t + 1].s;
       adj[(size_t)(F[t + 1].s * k + F[t + 1].f)] = (int)F[t].s;
@@ -646,6 +694,27 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   std::vector<int> hadj;
   int rc = build_adjacency(sv, m, hs, hadj);
   if (rc) return rc;
+  // split (Alg. 5): the boundary triangles (tetrahedron faces without a neighbour)
+  // with the tetrahedron each belongs to, and their edge adjacency (edges shared by
+  // more than two boundary triangles are left unpaired: every boundary triangle is
+  // seeded on its own, so the boundary pass covers it without them)
+  std::vector<int> bs, bt, badj;
+  c->split_ok = false;
+  if (mode == VD_MODE_3D && c->dtype == VD_F32) {
+    for (long long a = 0; a < m; ++a)
+      for (int f = 0; f < 4; ++f)
+        if (hadj[(size_t)(4 * a + f)] < 0) {
+          for (int l = 0; l < 4; ++l)
+            if (l != f) bs.push_back(hs[(size_t)(4 * a + l)]);
+          bt.push_back((int)a);
+        }
+    c->mb = (long long)bt.size();
+    if (c->mb > 0) {
+      build_adjacency(3, c->mb, bs, badj, /*strict=*/false);
+      c->split_ok = true;
+    }
+    for (int d = 0; d < 3; ++d) { c->mlo[d] = (float)lo[d]; c->mhi[d] = (float)hi[d]; }
+  }
   // device copies of the mesh
   {
     char* p = nullptr;
@@ -663,6 +732,15 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   CK(cudaMemcpy(c->fsgn, fs.data(), fs.size(), cudaMemcpyHostToDevice));
   DALLOC(c->tsgn, signed char, m, true);
   CK(cudaMemcpy(c->tsgn, orient.data(), orient.size(), cudaMemcpyHostToDevice));
+  if (c->split_ok) {
+    DALLOC(c->bsimp, int, bs.size(), true);
+    DALLOC(c->badj, int, badj.size(), true);
+    DALLOC(c->btet, int, bt.size(), true);
+    DALLOC(c->bnd, int, c->n, true);
+    CK(cudaMemcpy(c->bsimp, bs.data(), bs.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->badj, badj.data(), badj.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->btet, bt.data(), bt.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   // simplex locator: bins over the mesh box, each listing the simplices whose box meets it
   if (mode != VD_MODE_SURFACE) {
     int dims = mode == VD_MODE_2D ? 2 : 3;
@@ -835,7 +913,7 @@ static int autotune(vd_ctx* c) {
   int cand_m[8], cand_c[8], nc = 0;
   const int chunks[2] = {1, 4};
   for (int m = 1; m <= 2; ++m) {
-    if (m == 2 && (c->flood_grid_t == 0 || c->box)) continue;
+    if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c))) continue;
     if (c->opt.chunk > 0) { cand_m[nc] = m; cand_c[nc++] = std::min(c->opt.chunk, 64); continue; }
     for (int k = 0; k < 2; ++k) { cand_m[nc] = m; cand_c[nc++] = chunks[k]; }
   }

@@ -72,6 +72,10 @@ __device__ __forceinline__ void face_verts(int f, int& a0, int& a1, int& a2) {
   a2 = f <= 2 ? 3 : 2;
 }
 
+// pairs whose polytope starts as the box [blo, bhi]: every pair of the box form,
+// and the whole-cell pairs (m, i) of the split
+__device__ __forceinline__ bool box_pair(const Dev<float>& C, int a) { return C.box || a == C.m; }
+
 // box face f (axis f/2, lower bound for even f): inside is n.x <= c
 __device__ __forceinline__ void plane_box(const Dev<float>& C, int f, float3 vi, float4& P, float2& M) {
   int ax = f >> 1;
@@ -84,7 +88,7 @@ __device__ __forceinline__ void plane_box(const Dev<float>& C, int f, float3 vi,
 }
 
 __device__ void plane_face(const Dev<float>& C, int a, int f, float3 vi, float4& P, float2& M) {
-  if (C.box) { plane_box(C, f, vi, P, M); return; }
+  if (box_pair(C, a)) { plane_box(C, f, vi, P, M); return; }
   int l0, l1, l2;
   face_verts(f, l0, l1, l2);
   const int* s = C.simp + 4 * a;
@@ -120,7 +124,7 @@ __device__ __noinline__ ePlane eplane(const Dev<float>& C, int a, int i, int src
     return p;
   }
   int f = -1 - src, l0, l1, l2;
-  if (C.box) {
+  if (box_pair(C, a)) {
     int ax = f >> 1;
     double sg = (f & 1) ? 1.0 : -1.0;
     double b = (f & 1) ? (double)C.bhi[ax] : (double)C.blo[ax];
@@ -580,7 +584,7 @@ __device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Mask
     float4 q;
     if (sr[2] < 0) {
       float qx, qy, qz;
-      if (C.box) {  // box vertex: one face per axis
+      if (box_pair(C, a)) {  // box vertex: one face per axis
         float b[3];
         for (int u = 0; u < 3; ++u) {
           int f = -1 - sr[u];
@@ -715,7 +719,7 @@ __device__ void init_box(const Dev<float>& C, Warp3& W, Masks& Mk, float3 vi, in
 }
 
 __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, float3 vi, int lane) {
-  if (C.box) { init_box(C, W, Mk, vi, lane); return; }
+  if (box_pair(C, a)) { init_box(C, W, Mk, vi, lane); return; }
   if (lane < 4) {
     float4 P;
     float2 M;
@@ -743,7 +747,7 @@ __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i,
 
 #ifdef VD_PROFILE
 #define PROF_T0() long long _t0 = clock64()
-#define PROF_ADD(k) do { long long _t1 = clock64(); if (lane == 0) atomicAdd(C.stats + 24 + (k), (unsigned long long)(_t1 - _t0)); _t0 = _t1; } while (0)
+#define PROF_ADD(k) do { long long _t1 = clock64(); if (lane == 0) atomicAdd(C.stats + VD_STAT_DIAG + (k), (unsigned long long)(_t1 - _t0)); _t0 = _t1; } while (0)
 #else
 #define PROF_T0() do {} while (0)
 #define PROF_ADD(k) do {} while (0)
@@ -758,8 +762,9 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   init_tet(C, W, Mk, a, i, vi, lane);
   // orientation of the dual mesh against space: with the corner table below, the
   // edge-term sum of integrate() has the sign of the tet's orientation
+  const bool bx = box_pair(C, a);
   float sigma = 1.f;  // the box's dual mesh is oriented like a positive tet
-  if (!C.box) {
+  if (!bx) {
     sigma = (float)C.tsgn[a];
   }
   bool empty = false;
@@ -842,8 +847,10 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
         int src = W.psrc[x];
         if (src >= 0) {
           myflag[h] = src;
-          if (!C.box) push_pair(C, a, src);  // the box form seeds every site itself
-        } else if (C.box) {
+          // the box form seeds every site itself; the split propagates through
+          // negative flags only (Alg. 5)
+          if (!bx && !C.split) push_pair(C, a, src);
+        } else if (bx) {
           myflag[h] = FLAG_BOUNDARY;
         } else {
           int b = C.adj[4 * a + (-1 - src)];

@@ -7,7 +7,7 @@
 namespace vd {
 
 // counters in Dev::ctr
-enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_N = 8 };
+enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_SEEDS = 4, CTR_N = 8 };
 
 template <typename T>
 struct Dev {
@@ -51,6 +51,10 @@ struct Dev {
   // +y, -z, +z
   int box;
   float blo[3], bhi[3];
+  // split (Alg. 5, 3D): pairs (m, i) are whole cells, the box [blo, bhi] (the mesh's
+  // bounding box) clipped by the site's bisectors; the pieces of per-tetrahedron
+  // pairs propagate through negative flags only
+  int split;
 };
 
 __device__ __forceinline__ unsigned long long pair_key(int a, int i) {

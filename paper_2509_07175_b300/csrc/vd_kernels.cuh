@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(co
 #endif
       unsigned long long key = wait_item(C, (long long)h, lane);
 #ifdef VD_PROFILE
-      if (lane == 0) atomicAdd(C.stats + 29, (unsigned long long)(clock64() - tw));
+      if (lane == 0) atomicAdd(C.stats + VD_STAT_DIAG + 5, (unsigned long long)(clock64() - tw));
 #endif
       if (key == EMPTY_KEY) { stop = true; break; }
       int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
@@ -420,6 +420,139 @@ template <typename T>
 __device__ __forceinline__ long long npairs(const Dev<T>& C) {
   unsigned long long t = C.ctr[CTR_TAIL];
   return (long long)(t < (unsigned long long)C.qcap ? t : (unsigned long long)C.qcap);
+}
+
+// ---------------------------------------------------------------------------
+// Split of the sites for 3D clipped diagrams (Alg. 5).  The restricted diagram
+// on the domain's boundary triangles (the surface form of the same clip kernel,
+// run first on the same pair set) finds the boundary sites: those whose cells
+// meet the boundary surface in positive area.  Every other site's cell lies
+// inside M when the site does (Omega_i is convex and does not cross the
+// boundary), and misses M when it does not.
+// ---------------------------------------------------------------------------
+// Boundary pass results (queue slots [0, tail) of S): mark the boundary sites and
+// collect the 3D seeds (tetrahedron incident to the triangle, site); CTR_SEEDS
+// counts them.
+__global__ void k_split_mark(const __grid_constant__ Dev<float> S, const int* btet, int* bnd,
+                             unsigned long long* seeds) {
+  long long np = npairs(S);
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p0 = (long long)blockIdx.x * blockDim.x; p0 < np; p0 += stride) {
+    long long p = p0 + threadIdx.x;
+    bool first = false;
+    if (p < np && S.pmeas[p] > 0.f) {
+      unsigned long long key = S.queue[p];
+      int b = (int)(key >> 32), j = (int)(key & 0xffffffffull);
+      first = atomicExch(bnd + j, 1) == 0;
+      unsigned long long t = atomicAdd(S.ctr + CTR_SEEDS, 1ull);
+      seeds[t] = pair_key(btet[b], j);
+    }
+    unsigned f = __ballot_sync(FULL, first);
+    if ((threadIdx.x & 31) == 0 && f) atomicAdd(S.stats + VD_STAT_BOUNDARY_SITES, (unsigned long long)__popc(f));
+  }
+}
+
+__global__ void k_split_push(const __grid_constant__ Dev<float> C, const unsigned long long* seeds) {
+  long long ns = (long long)C.ctr[CTR_SEEDS];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += (long long)gridDim.x * blockDim.x) {
+    unsigned long long key = seeds[t];
+    push_pair(C, (int)(key >> 32), (int)(key & 0xffffffffull));
+  }
+}
+
+// Sign of the orientation determinant of (a, b, c, d) (the volume of the
+// tetrahedron, times 6), evaluated in float64 from float32 coordinates; 0 when
+// it does not clear an error bound of 1e-12 times the permanent (the same
+// products on absolute values), several thousand times the standard forward
+// bound of this evaluation order, so a nonzero sign is certain.
+__device__ int orient3_sign(const float* a, const float* b, const float* c, const float* d) {
+  double adx = (double)a[0] - d[0], ady = (double)a[1] - d[1], adz = (double)a[2] - d[2];
+  double bdx = (double)b[0] - d[0], bdy = (double)b[1] - d[1], bdz = (double)b[2] - d[2];
+  double cdx = (double)c[0] - d[0], cdy = (double)c[1] - d[1], cdz = (double)c[2] - d[2];
+  double det = adx * (bdy * cdz - bdz * cdy) + bdx * (cdy * adz - cdz * ady) + cdx * (ady * bdz - adz * bdy);
+  double perm = fabs(adx) * (fabs(bdy * cdz) + fabs(bdz * cdy)) + fabs(bdx) * (fabs(cdy * adz) + fabs(cdz * ady)) +
+                fabs(cdx) * (fabs(ady * bdz) + fabs(adz * bdy));
+  double eb = 1e-12 * perm;
+  return det > eb ? 1 : (det < -eb ? -1 : 0);
+}
+
+// The same determinant in float32 with its permanent: Shewchuk's forward bound for
+// this evaluation from float inputs is below 5e-7 of the permanent, so a value
+// beyond 1e-5 of it has a certain sign.
+__device__ __forceinline__ float orient3f(const float* a, const float* b, const float* c, const float* d,
+                                          float& perm) {
+  float adx = a[0] - d[0], ady = a[1] - d[1], adz = a[2] - d[2];
+  float bdx = b[0] - d[0], bdy = b[1] - d[1], bdz = b[2] - d[2];
+  float cdx = c[0] - d[0], cdy = c[1] - d[1], cdz = c[2] - d[2];
+  perm = fabsf(adx) * (fabsf(bdy * cdz) + fabsf(bdz * cdy)) + fabsf(bdx) * (fabsf(cdy * adz) + fabsf(cdz * ady)) +
+         fabsf(cdx) * (fabsf(ady * bdz) + fabsf(adz * bdy));
+  return adx * (bdy * cdz - bdz * cdy) + bdx * (cdy * adz - cdz * ady) + cdx * (ady * bdz - adz * bdy);
+}
+
+// Where site i lies w.r.t. tetrahedron a: 2 strictly inside (certain), 0 certainly
+// not inside, 1 undecided (on or within rounding of its boundary).  The point
+// replaces each vertex in turn; it is inside iff every such determinant has the
+// tetrahedron's orientation sign.  Float32 first, float64 where float32 cannot
+// certify the sign.
+__device__ __forceinline__ int tet_holds(const Dev<float>& C, int a, const float* p) {
+  float V[4][3];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float* q = C.verts + 3 * C.simp[4 * a + l];
+    V[l][0] = q[0]; V[l][1] = q[1]; V[l][2] = q[2];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {  // bounding box first (exact comparisons)
+    float lo = fminf(fminf(V[0][d], V[1][d]), fminf(V[2][d], V[3][d]));
+    float hi = fmaxf(fmaxf(V[0][d], V[1][d]), fmaxf(V[2][d], V[3][d]));
+    if (p[d] < lo || p[d] > hi) return 0;
+  }
+  // orient3f(a, b, c, d) = det[a - d, b - d, c - d] has the sign opposite to the
+  // volume of (a, b, c, d), whose sign is tsgn
+  const int o = -C.tsgn[a];
+  bool all = true;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const float* A = f == 0 ? p : V[0];
+    const float* B = f == 1 ? p : V[1];
+    const float* Cc = f == 2 ? p : V[2];
+    const float* D = f == 3 ? p : V[3];
+    float pm;
+    float x = orient3f(A, B, Cc, D, pm);
+    int sg = x > 1e-5f * pm ? 1 : (x < -1e-5f * pm ? -1 : orient3_sign(A, B, Cc, D));
+    if (sg == -o) return 0;
+    all = all && sg == o;
+  }
+  return all ? 2 : 1;
+}
+
+// Seeds of every site: a site that is not a boundary site and lies strictly in a
+// tetrahedron gets the whole-cell pair (m, i); any other site seeds every
+// tetrahedron that may hold it (with the boundary seeds these reach every piece
+// of a boundary site through negative flags).  A non-boundary site in no
+// tetrahedron has an empty cell and no pair.
+__global__ void k_split_site(const __grid_constant__ Dev<float> C, Locator L, const int* bnd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool whole = false;
+  if (i < C.n) {
+    const float* p = C.sites + 3 * i;
+    int bx = (int)floor(((double)p[0] - L.ox) * L.ih), by = (int)floor(((double)p[1] - L.oy) * L.ih),
+        bz = (int)floor(((double)p[2] - L.oz) * L.ih);
+    if (bx >= 0 && by >= 0 && bz >= 0 && bx < L.bx && by < L.by && bz < L.bz) {
+      int b = (bz * L.by + by) * L.bx + bx;
+      int t0 = L.start[b], t1 = L.start[b + 1];
+      if (!bnd[i])
+        for (int t = t0; t < t1 && !whole; ++t) whole = tet_holds(C, L.items[t], p) == 2;
+      if (whole) {
+        push_pair(C, C.m, i);
+      } else {
+        for (int t = t0; t < t1; ++t)
+          if (tet_holds(C, L.items[t], p)) push_pair(C, L.items[t], i);
+      }
+    }
+  }
+  unsigned w = __ballot_sync(FULL, whole);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(C.stats + VD_STAT_WHOLE_CELLS, (unsigned long long)__popc(w));
 }
 
 template <typename T>

@@ -142,7 +142,10 @@ def shell_domain(ncube: int = 32, seed: int = SEED_BASE + 3, jitter: float = 0.0
     into 6 Kuhn tets (172,032 tets), maps every vertex x -> x |x|_inf / |x|_2
     (the L-inf shell onto the Euclidean shell) and jitters the interior
     vertices by U[-jitter*h, jitter*h] per coordinate (h = 2/ncube).  Vertices
-    are rounded to float32; every tet keeps a positive volume.
+    are rounded to float32.  The tets keep the orientation of the unjittered
+    mesh (a proper tetrahedralisation of the region), and a vertex whose jitter
+    would invert one of its tets stays unjittered: re-orienting an inverted tet
+    would fold it over its neighbours, so that tets overlap.
     """
     h = 2.0 / ncube
     lo_in = int(round(0.5 / h))  # number of cubes from -1 to -0.5
@@ -159,14 +162,18 @@ def shell_domain(ncube: int = 32, seed: int = SEED_BASE + 3, jitter: float = 0.0
     l2 = np.linalg.norm(verts, axis=1)
     verts = verts * (linf / l2)[:, None]
     interior = (np.abs(linf - 0.5) > 1e-12) & (np.abs(linf - 1.0) > 1e-12)
-    rng = _rng(seed)
-    jit = rng.uniform(-jitter * h, jitter * h, size=verts.shape)
-    verts = verts + jit * interior[:, None]
-    verts = verts.astype(np.float32).astype(np.float64)
     tets = _orient_tets(verts, tets)
-    vol = _tet_volumes(verts, tets)
+    rng = _rng(seed)
+    jit = rng.uniform(-jitter * h, jitter * h, size=verts.shape) * interior[:, None]
+    for _ in range(64):
+        vj = (verts + jit).astype(np.float32).astype(np.float64)
+        bad = _tet_volumes(vj, tets) <= 0
+        if not bad.any():
+            break
+        jit[np.unique(tets[bad])] = 0.0
+    vol = _tet_volumes(vj, tets)
     assert (vol > 0).all(), "shell tet with non-positive volume"
-    return verts, tets
+    return vj, tets
 
 
 def torus_domain(nu: int = 1000, nv: int = 250, R: float = 1.0, r: float = 0.3,

@@ -7,6 +7,8 @@
                   (--proposal mlp trains it first on labels from plain computes
                   of seeded 100k-site cube instances, --train-epochs epochs)
 --mapping 0|1|2   clip kernel: autotuned, warp per pair, thread per pair
+--split           3D: interior sites' cells computed whole after the boundary
+                  pass (Alg. 5); the others per tetrahedron
 
 One JSON line per compute: phase times (CUDA events), clip-kernel mapping and
 the work counters.  Every compute runs the whole path through the C ABI.
@@ -31,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--mapping", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--chunk", type=int, default=1)
     ap.add_argument("--train-epochs", type=int, default=None)
+    ap.add_argument("--split", action="store_true")
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args(argv)
 
@@ -47,7 +50,7 @@ def main(argv=None):
         print(json.dumps({"training": {"rows": tr["rows"], "epochs": tr["epochs"], "train_s": tr["train_s"],
                                        "loss": tr["epoch_loss"][-1]}}), flush=True)
     d.set_options(learned=int(args.form == "learned"), topk=args.topk, proposal=prop, mapping=args.mapping,
-                  chunk=args.chunk, stats=1, timing=1)
+                  chunk=args.chunk, stats=1, timing=1, split=int(args.split))
     for k in range(args.repeat):
         r = d.compute()
         s = r["stats"]
@@ -57,7 +60,8 @@ def main(argv=None):
                           "mapping": s["mapping"], "chunk": s["chunk"],
                           "stats": {key: s[key] for key in ("pairs", "nonempty", "nn_queries", "corner_tests",
                                                             "clips", "search_steps", "sites_scanned",
-                                                            "learned_hits", "list_tests", "fp64", "uncertain")}}),
+                                                            "learned_hits", "list_tests", "fp64", "uncertain",
+                                                            "whole_cells", "boundary_sites")}}),
               flush=True)
     d.close()
 

@@ -36,12 +36,29 @@ def gpu_csr(r):
     return [list(map(int, idx[off[i]:off[i + 1]])) for i in range(len(off) - 1)]
 
 
-def compare_full(w, r, p, oracle_pieces, sites_subset=None, meas_floor=0.0):
+def whole_cell_topology(ot, gt, m):
+    """The oracle's per-simplex topology with the pieces of every site that the GPU
+    computed as one whole cell (piece (m, i), the split of Alg. 5) merged into
+    (m, i): the union of their bisector flags.  Such a cell must lie inside the
+    domain: none of its oracle pieces has a face on the domain boundary."""
+    whole = {i for (a, i) in gt if a == m}
+    out = {}
+    for (a, i), fl in ot.items():
+        if i in whole:
+            assert O.FLAG_BOUNDARY not in fl, f"site {i} computed whole but its cell meets the boundary"
+            out.setdefault((m, i), set()).update(f for f in fl if f >= 0)
+        else:
+            out[(a, i)] = fl
+    return {k: tuple(sorted(v)) if isinstance(v, set) else v for k, v in out.items()}
+
+
+def compare_full(w, r, p, oracle_pieces, sites_subset=None, meas_floor=0.0, split=False):
     """Bit-exact topology and neighbours; measures / centroids within tolerance.
 
     meas_floor > 0: measures are compared relative to max(m, meas_floor) (cells
     reaching into the domain from far away are computed in the frame of their
-    site, whose FP32 error scales with the distance, not with the piece)."""
+    site, whose FP32 error scales with the distance, not with the piece).
+    split: whole-cell pieces (m, i) stand for all of the site's oracle pieces."""
     n = len(w["sites"])
     om, oc, onb = O.per_site(n, w["sites"], oracle_pieces)
     gm = r["measure"].double().cpu().numpy()
@@ -50,6 +67,8 @@ def compare_full(w, r, p, oracle_pieces, sites_subset=None, meas_floor=0.0):
     ids = np.arange(n) if sites_subset is None else np.asarray(sites_subset)
     ot = oracle_pieces.topology()
     gt = gpu_topology(p)
+    if split:
+        ot = whole_cell_topology(ot, gt, len(w["simp"]))
     if sites_subset is not None:
         s = set(int(x) for x in ids)
         gt = {k: v for k, v in gt.items() if k[1] in s}
