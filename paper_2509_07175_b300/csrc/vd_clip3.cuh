@@ -399,22 +399,30 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
   int base = inc - cnt;
   int total = __shfl_sync(FULL, inc, 31);
   if (total > nfree || total < 3) { set_error(C.status, total < 3 ? VD_ERR_LIMIT : VD_ERR_CAPACITY); return -1; }
-  // reset the loop maps, then claim them
+  // Edge k of the boundary (in lane order) takes the k-th free slot; the edges are
+  // spread over the lanes through shared memory (the integration scratch, unused
+  // until the polytope is final) so that each lane claims and builds one new
+  // corner instead of the owner of a removed corner building all of its edges.
+  unsigned* ebuf = reinterpret_cast<unsigned*>(W.contrib);
+  int* sbuf = reinterpret_cast<int*>(ebuf + MAXT);
   __syncwarp();
 #pragma unroll 1
-  for (int c = 0; c < cnt; ++c) { W.stri[edge[c] & 255u] = -1; W.etri[(edge[c] >> 8) & 255u] = -1; }
+  for (int c = 0; c < cnt; ++c) ebuf[base + c] = edge[c];
+  __syncwarp();
+  // reset the loop maps, then claim them
+#pragma unroll 1
+  for (int k = lane; k < total; k += 32) { unsigned e = ebuf[k]; W.stri[e & 255u] = -1; W.etri[(e >> 8) & 255u] = -1; }
   __syncwarp();
   int c0 = __popc(fr[0]), c1 = __popc(fr[1]);
   bool bad = false;
   unsigned newm[3] = {0, 0, 0};
-  int slot[9];
 #pragma unroll 1
-  for (int c = 0; c < cnt; ++c) {
-    int k = base + c;
+  for (int k = lane; k < total; k += 32) {
+    unsigned e = ebuf[k];
     int sl = k < c0 ? nth_set(fr[0], k) : (k < c0 + c1 ? 32 + nth_set(fr[1], k - c0) : 64 + nth_set(fr[2], k - c0 - c1));
-    slot[c] = sl;
-    if (atomicExch(&W.stri[edge[c] & 255u], sl) != -1) bad = true;
-    if (atomicExch(&W.etri[(edge[c] >> 8) & 255u], sl) != -1) bad = true;
+    sbuf[k] = sl;
+    if (atomicExch(&W.stri[e & 255u], sl) != -1) bad = true;
+    if (atomicExch(&W.etri[(e >> 8) & 255u], sl) != -1) bad = true;
   }
   if (__any_sync(FULL, bad)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
   __syncwarp();
@@ -422,8 +430,9 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
   float4 Pn = W.pn[pl];
   float2 Mn = W.pm[pl];
 #pragma unroll 1
-  for (int c = 0; c < cnt; ++c) {
-    int sl = slot[c], x = edge[c] & 255u, y = (edge[c] >> 8) & 255u, u = edge[c] >> 16;
+  for (int k = lane; k < total; k += 32) {
+    unsigned e = ebuf[k];
+    int sl = sbuf[k], x = e & 255u, y = (e >> 8) & 255u, u = e >> 16;
     W.tv[sl] = make_uchar4((unsigned char)x, (unsigned char)y, (unsigned char)pl, 0);
     W.tn[sl] = make_uchar4((unsigned char)u, (unsigned char)W.stri[y], (unsigned char)W.etri[x], 0);
     uchar4 uv = W.tv[u];
@@ -436,7 +445,10 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
       qc = refine64(C, a, i, W.psrc[x], W.psrc[y], W.psrc[pl]);
     W.tq[sl] = qc;
     W.twit[sl] = -1;
-    newm[sl >> 5] |= 1u << (sl & 31);
+    unsigned b = 1u << (sl & 31);
+    newm[0] |= sl < 32 ? b : 0u;
+    newm[1] |= (sl >> 5) == 1 ? b : 0u;
+    newm[2] |= sl >= 64 ? b : 0u;
   }
   __syncwarp();
   if (__any_sync(FULL, bad)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
