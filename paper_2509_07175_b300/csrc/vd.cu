@@ -94,6 +94,7 @@ struct vd_ctx {
   int flood_grid = 0;
   size_t flood_smem = 0;
   int flood_grid_t = 0;           // thread-per-pair kernel (3D FP32)
+  int knn_grid = 0;               // resident blocks of k_knn on the device
   int cur_mapping = 1, cur_chunk = 1;  // used by the next enqueue
   bool tuned = false;             // autotuned choice cached for the current domain and options
   int tuned_mapping = 1, tuned_chunk = 1;
@@ -290,7 +291,7 @@ static void enqueue_compute(vd_ctx* c) {
   c->launches += 1;
   if (c->opt.learned && !c->cand) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
-    k_knn<T><<<c->nsm * 8, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
     if (c->opt.proposal == VD_PROPOSAL_MLP)
       mlp::k_mlp_rank<T><<<c->nsm * MLP_RANK_BLOCKS, 128, sizeof(mlp::RankSmem), s>>>(
           D, c->knn, (const T*)c->delta, c->mlp_wb, c->mlp_p, c->opt.topk, c->cmask);
@@ -390,6 +391,9 @@ static int flood_config(vd_ctx* c) {
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood<T, MODE>, FLOOD_WARPS * 32, c->flood_smem));
   c->flood_grid = std::max(1, per_sm) * c->nsm;
+  int per_sm_k = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_k, k_knn<T>, KNN_WARPS * 32, 0));
+  c->knn_grid = std::max(1, per_sm_k) * c->nsm;
   c->flood_grid_t = 0;
   c->flood_grid_s = 0;
   if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) {
@@ -1258,7 +1262,7 @@ int mlp_features_t(vd_ctx* c, void* x, uint32_t* labels) {
   cudaStream_t s = c->stream;
   Dev<T> D = make_dev<T>(c);
   if (!c->knn_fresh) {
-    k_knn<T><<<c->nsm * 8, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
     c->knn_fresh = true;
   }
   if (x)

@@ -108,10 +108,13 @@ __global__ void k_query_level(int G0, const int* cstart0, unsigned char* qlev, i
 // delta_i = half the distance from v_i to its nearest other site (Sec. 5.1)
 template <typename T>
 __global__ void k_delta(const __grid_constant__ Dev<T> C, T* delta) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C.n) return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C.n) return;
+  // sites in the grid's cell order: neighbouring threads query neighbouring cells
+  const typename Prec<T>::V4 s = C.G.L[0].gs[t];
+  int i = site_id(s);
   T d2;
-  int k = thread_nearest(C.G, C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2], i, d2);
+  int k = thread_nearest(C.G, s.x, s.y, s.z, i, d2);
   if (k >= 0 && k < C.n && d2 == T(0)) set_error(C.status, VD_ERR_DUPLICATE);  // coincident sites
   delta[i] = (k >= 0 && k < C.n) ? T(0.5) * sqrt(d2) : T(1);
 }
@@ -161,12 +164,14 @@ __global__ void k_power_lift(const float* xy, const float* w, long long n, const
   out[3 * t + 2] = sqrtf(eta - wt);
 }
 
-// box domain: every site's cell is one piece, (0, i); no pair set is needed
+// box domain: every site's cell is one piece, (0, i); no pair set is needed.  The
+// queue follows the grid's cell order, so that pairs processed at the same time
+// are neighbours and share their grid cells and lists in the caches.
 __global__ void k_seed_box(Dev<float> C) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C.n) return;
-  C.queue[i] = pair_key(0, i);
-  if (i == 0) atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)C.n);
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C.n) return;
+  C.queue[t] = pair_key(0, site_id(C.G.L[0].gs[t]));
+  if (t == 0) atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)C.n);
 }
 
 struct Locator {
@@ -194,9 +199,11 @@ __device__ __forceinline__ R orient2(const R* a, const R* b, const R* p) {
 // of the simplex for FP32: a site within that of a face may seed either side.
 template <typename T>
 __global__ void k_seed_site(const __grid_constant__ Dev<T> C, Locator L) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C.n) return;
-  T p[3] = {C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]};
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C.n) return;
+  const typename Prec<T>::V4 s4 = C.G.L[0].gs[t];  // grid cell order (see k_seed_box)
+  int i = site_id(s4);
+  T p[3] = {s4.x, s4.y, s4.z};
   int bx = (int)floor(((double)p[0] - L.ox) * L.ih), by = (int)floor(((double)p[1] - L.oy) * L.ih),
       bz = (int)floor(((double)p[2] - L.oz) * L.ih);
   if (bx < 0 || by < 0 || bz < 0 || bx >= L.bx || by >= L.by || bz >= L.bz) return;
@@ -330,34 +337,137 @@ __global__ void __launch_bounds__(FLOOD_T_THREADS, FLOOD_T_MIN_BLOCKS) k_flood_t
 // the 32 nearest other sites of every site (features of the learned proposal)
 // ---------------------------------------------------------------------------
 constexpr int KNN = 32;
-constexpr int KNN_CAP = 1024;
+constexpr int KNN_SLOTS = 32;  // stored sites per lane (1024 per site)
 constexpr int KNN_WARPS = 4;
 
 struct KnnScratch {
-  float d2[KNN_CAP];
-  int id[KNN_CAP];
-  int cnt;
-  ScanScratch ss;  // segment table of rings beyond ring 1
+  float d2[KNN_SLOTS][WARP];  // [slot][lane]: each lane appends to its own column
+  int id[KNN_SLOTS][WARP];
+  ScanScratch ss;             // segment table of rings beyond ring 1
 };
 
-// warp per site: collect the sites of growing rings around v_i, then select the
-// 32 smallest squared distances (ties: smaller index) once the 32nd is covered
+// Ring r of level 0 or a hashed level (r = 1: the 3x3x3 block), flattened over
+// the lanes like the rings of the clip kernel's scans, restricted to the cells that meet
+// the ball of squared radius r2 around q (a ring cell or row farther away cannot
+// hold one of the 32 nearest once 32 sites within sqrt(r2) are known).  Cell
+// bounds are widened by 1e-4 of the edge, and the outer side of a level-0
+// boundary row is open (sites beyond the grid box are kept in boundary cells).
+template <typename T, typename Visit>
+__device__ __noinline__ void knn_scan_shell(const GridView<T>& G, int lev, int cx, int cy, int cz, int r, int lane,
+                                            ScanScratch& S, Visit& visit, T qx, T qy, T qz, T r2) {
+  const T h = G.L[lev].h, slack = T(1e-4) * h;
+  auto gap = [&](T q, T lo, bool has_lo, bool has_hi) {
+    T g = T(0);
+    if (has_lo) g = fmax(g, (lo - slack) - q);
+    if (has_hi) g = fmax(g, q - (lo + h + slack));
+    return g;
+  };
+  int nslots = ring_slots(lev, r);
+  const typename Prec<T>::V4* gs = G.L[lev].gs;
+  for (int base = 0; base < nslots; base += WARP) {
+    int b = 0, e = 0;
+    int slot = base + lane;
+    if (slot < nslots) {
+      int side = 2 * r + 1;
+      if (lev > 0) {
+        int dx = slot % side - r, t = slot / side;
+        int dy = t % side - r, dz = t / side - r;
+        bool inner = r > 1 && dx > -r && dx < r && dy > -r && dy < r && dz > -r && dz < r;
+        if (slot < side * side * side && !inner) {
+          T gx_ = gap(qx, G.ox + T(cx + dx) * h, true, true), gy_ = gap(qy, G.oy + T(cy + dy) * h, true, true),
+            gz_ = gap(qz, G.oz + T(cz + dz) * h, true, true);
+          if (gx_ * gx_ + gy_ * gy_ + gz_ * gz_ <= r2) {
+            unsigned k = cell_hash(cx + dx, cy + dy, cz + dz) & G.L[lev].mask;
+            b = __ldg(G.L[lev].start + k);
+            e = __ldg(G.L[lev].start + k + 1);
+          }
+        }
+      } else {
+        int row = slot >> 1, half = slot & 1;
+        int dy = row % side - r, dz = row / side - r;
+        int y = cy + dy, z = cz + dz;
+        if (row < side * side && y >= 0 && y < G.gy && z >= 0 && z < G.gz) {
+          bool full = r == 1 || dy == r || dy == -r || dz == r || dz == -r;
+          int x0 = -1, x1 = -2;
+          if (full) { if (!half) { x0 = cx - r; x1 = cx + r; } }
+          else x0 = x1 = half ? cx + r : cx - r;
+          x0 = x0 < 0 ? 0 : x0;
+          x1 = x1 > G.gx - 1 ? G.gx - 1 : x1;
+          T gy_ = gap(qy, G.oy + T(y) * h, y > 0, y < G.gy - 1), gz_ = gap(qz, G.oz + T(z) * h, z > 0, z < G.gz - 1);
+          T rem = r2 - gy_ * gy_ - gz_ * gz_;
+          if (x0 <= x1 && rem >= T(0)) {
+            T w = sqrt(rem) + slack;
+            T fa = (qx - w - G.ox) * G.L[0].ih, fb = (qx + w - G.ox) * G.L[0].ih;
+            if (fa > T(x0)) x0 = fa >= T(x1 + 1) ? x1 + 1 : (int)floor(fa);
+            if (fb < T(x1)) x1 = fb < T(x0) ? x0 - 1 : (int)floor(fb);
+            if (x0 <= x1) {
+              int rb = (z * G.gy + y) * G.gx;
+              b = __ldg(G.L[0].start + rb + x0);
+              e = __ldg(G.L[0].start + rb + x1 + 1);
+            }
+          }
+        }
+      }
+    }
+    int incl = warp_incl_scan(e - b, lane);
+    int total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) continue;
+    __syncwarp();
+    S.seg_b[lane] = b;
+    S.seg_i[lane] = incl;
+    __syncwarp();
+    for (int f0 = 0; f0 < total; f0 += WARP) {
+      int f = f0 + lane;
+      if (f < total) {
+        int lo = 0, hi = WARP - 1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (S.seg_i[mid] > f) hi = mid; else lo = mid + 1;
+        }
+        int excl = lo ? S.seg_i[lo - 1] : 0;
+        visit(gs[S.seg_b[lo] + (f - excl)]);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Warp per site: collect the sites of growing rings around v_i (each lane keeps
+// the sites it meets in its own column of shared memory), then merge the lanes'
+// sorted columns into the 32 nearest (ties: smaller index).  After the first
+// ring, a radius that already holds 32 collected sites bounds the rest of the
+// scan.
 template <typename T>
 __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ Dev<T> C, int* knn, float* knn_d2) {
   __shared__ KnnScratch sh[KNN_WARPS];
   KnnScratch& S = sh[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = gw; i < C.n; i += nw) {
-    T qx = C.sites[3 * i], qy = C.sites[3 * i + 1], qz = C.sites[3 * i + 2];
-    if (lane == 0) S.cnt = 0;
-    __syncwarp();
+  // each block takes a contiguous range of the sites in the grid's cell order, its
+  // warps interleaved, so that a block's warps scan neighbouring cells
+  long long per = ((long long)C.n + gridDim.x - 1) / gridDim.x;
+  long long t0 = (long long)blockIdx.x * per, t1 = t0 + per < C.n ? t0 + per : C.n;
+  for (long long t = t0 + (threadIdx.x >> 5); t < t1; t += KNN_WARPS) {
+    const typename Prec<T>::V4 s4 = C.G.L[0].gs[t];
+    const int i = site_id(s4);
+    T qx = s4.x, qy = s4.y, qz = s4.z;
+    int cnt = 0;
+    bool over = false;
     auto visit = [&](const typename Prec<T>::V4& s) {
       int k = site_id(s);
       if (k == i) return;
       T dx = s.x - qx, dy = s.y - qy, dz = s.z - qz;
-      int slot = atomicAdd(&S.cnt, 1);
-      if (slot < KNN_CAP) { S.d2[slot] = (float)(dx * dx + dy * dy + dz * dz); S.id[slot] = k; }
+      if (cnt < KNN_SLOTS) {
+        S.d2[cnt][lane] = (float)(dx * dx + dy * dy + dz * dz);
+        S.id[cnt][lane] = k;
+        ++cnt;
+      } else {
+        over = true;
+      }
+    };
+    auto count_below = [&](float lim) {
+      int c = 0;
+      for (int t = 0; t < cnt; ++t) c += S.d2[t][lane] <= lim;
+      return (int)__reduce_add_sync(FULL, (unsigned)c);
     };
     int lev = C.G.query_level(qx, qy, qz), cx, cy, cz;
     C.G.cell_at(lev, qx, qy, qz, cx, cy, cz);
@@ -365,44 +475,61 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     // the stored distances are below cover^2 (so no unseen site can be nearer
     // than the 32nd); otherwise the list is kept for the features but flagged
     bool certified = false;
+    T bound2 = T(1e36);  // squared radius holding 32 collected sites (after ring 1)
     for (int r = 1;; ++r) {
-      warp_scan_ring(C.G, lev, cx, cy, cz, r, lane, S.ss, visit);
+      knn_scan_shell(C.G, lev, cx, cy, cz, r, lane, S.ss, visit, qx, qy, qz, bound2);
       __syncwarp();
-      int cnt = min(S.cnt, KNN_CAP);
+      if (__any_sync(FULL, over)) break;
       T m = C.G.cover(lev, cx, cy, cz, r, qx, qy, qz);
-      if (S.cnt > KNN_CAP) break;
       if (m >= T(1e29)) { certified = true; break; }
-      if (cnt >= KNN) {
+      int total = (int)__reduce_add_sync(FULL, (unsigned)cnt);
+      if (total >= KNN) {
         float m2 = (float)(m * m) * (1.f - 1e-5f);
-        int below = 0;
-        for (int t = lane; t < cnt; t += 32) below += S.d2[t] <= m2;
-        below = __reduce_add_sync(FULL, below);
-        if (below >= KNN) { certified = true; break; }
+        if (count_below(m2) >= KNN) { certified = true; break; }
+        if (r == 1) {
+          // a radius with 32 collected sites within it: the largest of each lane's
+          // distances bounds its column, so grow a guess from the cover until the
+          // count reaches 32 (at worst the largest collected distance)
+          float top = 0.f;
+          for (int t = 0; t < cnt; ++t) top = fmaxf(top, S.d2[t][lane]);
+          top = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(top)));
+          float g = m2 > 0.f ? m2 : top;
+          while (g < top && count_below(g) < KNN) g = fminf(top, 2.f * g);
+          bound2 = (T)g * T(1.0001);
+        }
       }
       if (r >= 4) break;
     }
-    int cnt = min(S.cnt, KNN_CAP);
     __syncwarp();
-    // selection of the 32 nearest, in order
-    for (int k = 0; k < KNN; ++k) {
-      float bd = 3.0e38f;
-      int bi = 0x7fffffff, bs = -1;
-      for (int t = lane; t < cnt; t += 32) {
-        float d = S.d2[t];
-        int id = S.id[t];
-        if (d < bd || (d == bd && id < bi)) { bd = d; bi = id; bs = t; }
+    // each lane sorts its column (insertion sort; ties by index), then 32 rounds
+    // of a warp-wide minimum over the column heads
+    for (int u = 1; u < cnt; ++u) {
+      float du = S.d2[u][lane];
+      int iu = S.id[u][lane];
+      int v = u - 1;
+      while (v >= 0 && (S.d2[v][lane] > du || (S.d2[v][lane] == du && S.id[v][lane] > iu))) {
+        S.d2[v + 1][lane] = S.d2[v][lane];
+        S.id[v + 1][lane] = S.id[v][lane];
+        --v;
       }
+      S.d2[v + 1][lane] = du;
+      S.id[v + 1][lane] = iu;
+    }
+    int head = 0;
+    for (int k = 0; k < KNN; ++k) {
+      float bd = head < cnt ? S.d2[head][lane] : 3.0e38f;
+      int bi = head < cnt ? S.id[head][lane] : 0x7fffffff;
       float d0 = bd;
       int i0 = bi;
       warp_argmin(bd, bi);
-      if (d0 == bd && i0 == bi && bs >= 0) S.d2[bs] = 3.0e38f;
+      if (d0 == bd && i0 == bi && head < cnt) ++head;
       if (lane == 0) {
         knn[(long long)i * KNN + k] = bi == 0x7fffffff ? -1 : bi;
         // a negative 32nd distance marks a list that is not certified complete
         knn_d2[(long long)i * KNN + k] = (k == KNN - 1 && !certified) ? -1.f : bd;
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
 }
 
@@ -532,9 +659,10 @@ __device__ __forceinline__ int tet_holds(const Dev<float>& C, int a, const float
 // of a boundary site through negative flags).  A non-boundary site in no
 // tetrahedron has an empty cell and no pair.
 __global__ void k_split_site(const __grid_constant__ Dev<float> C, Locator L, const int* bnd) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
   bool whole = false;
-  if (i < C.n) {
+  if (t < C.n) {
+    const int i = site_id(C.G.L[0].gs[t]);  // grid cell order (see k_seed_box)
     const float* p = C.sites + 3 * i;
     int bx = (int)floor(((double)p[0] - L.ox) * L.ih), by = (int)floor(((double)p[1] - L.oy) * L.ih),
         bz = (int)floor(((double)p[2] - L.oz) * L.ih);
