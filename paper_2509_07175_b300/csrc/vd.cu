@@ -287,11 +287,15 @@ static void enqueue_compute(vd_ctx* c) {
     }
   }
   mark(c, 1);
-  k_delta<T><<<nblk(c->n, 128), 128, 0, s>>>(D, (T*)c->delta);
-  c->launches += 1;
+  // learned form (FP32): the 32-nearest pass also yields delta_i
+  const bool fused = c->opt.learned && !c->cand && std::is_same<T, float>::value;
+  if (!fused) {
+    k_delta<T><<<nblk(c->n, 128), 128, 0, s>>>(D, (T*)c->delta);
+    c->launches += 1;
+  }
   if (c->opt.learned && !c->cand) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
-    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, fused ? (T*)c->delta : nullptr);
     if (c->opt.proposal == VD_PROPOSAL_MLP)
       mlp::k_mlp_rank<T><<<c->nsm * MLP_RANK_BLOCKS, 128, sizeof(mlp::RankSmem), s>>>(
           D, c->knn, (const T*)c->delta, c->mlp_wb, c->mlp_p, c->opt.topk, c->cmask);
@@ -1262,7 +1266,7 @@ int mlp_features_t(vd_ctx* c, void* x, uint32_t* labels) {
   cudaStream_t s = c->stream;
   Dev<T> D = make_dev<T>(c);
   if (!c->knn_fresh) {
-    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, nullptr);
     c->knn_fresh = true;
   }
   if (x)

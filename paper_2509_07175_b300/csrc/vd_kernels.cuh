@@ -437,8 +437,12 @@ __device__ __noinline__ void knn_scan_shell(const GridView<T>& G, int lev, int c
 // sorted columns into the 32 nearest (ties: smaller index).  After the first
 // ring, a radius that already holds 32 collected sites bounds the rest of the
 // scan.
+// delta (optional): also writes delta_i (Sec. 5.1) from the list's first entry when
+// the scan certifies it as the nearest site, with the checks of k_delta; a site whose
+// nearest is not certified by the scan gets its own nearest-site query.
 template <typename T>
-__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ Dev<T> C, int* knn, float* knn_d2) {
+__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ Dev<T> C, int* knn, float* knn_d2,
+                                                        T* delta) {
   __shared__ KnnScratch sh[KNN_WARPS];
   KnnScratch& S = sh[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
@@ -476,11 +480,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     // than the 32nd); otherwise the list is kept for the features but flagged
     bool certified = false;
     T bound2 = T(1e36);  // squared radius holding 32 collected sites (after ring 1)
+    T covered = T(0);    // every site within this distance of v_i has been collected
     for (int r = 1;; ++r) {
       knn_scan_shell(C.G, lev, cx, cy, cz, r, lane, S.ss, visit, qx, qy, qz, bound2);
       __syncwarp();
       if (__any_sync(FULL, over)) break;
       T m = C.G.cover(lev, cx, cy, cz, r, qx, qy, qz);
+      covered = r == 1 || bound2 > m * m ? m : sqrt(bound2);
       if (m >= T(1e29)) { certified = true; break; }
       int total = (int)__reduce_add_sync(FULL, (unsigned)cnt);
       if (total >= KNN) {
@@ -516,6 +522,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
       S.id[v + 1][lane] = iu;
     }
     int head = 0;
+    float near2 = 3.0e38f;
+    int near = 0x7fffffff;
     for (int k = 0; k < KNN; ++k) {
       float bd = head < cnt ? S.d2[head][lane] : 3.0e38f;
       int bi = head < cnt ? S.id[head][lane] : 0x7fffffff;
@@ -523,10 +531,26 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
       int i0 = bi;
       warp_argmin(bd, bi);
       if (d0 == bd && i0 == bi && head < cnt) ++head;
+      if (k == 0) { near2 = bd; near = bi; }
       if (lane == 0) {
         knn[(long long)i * KNN + k] = bi == 0x7fffffff ? -1 : bi;
         // a negative 32nd distance marks a list that is not certified complete
         knn_d2[(long long)i * KNN + k] = (k == KNN - 1 && !certified) ? -1.f : bd;
+      }
+    }
+    if (delta && lane == 0) {
+      // the first entry is the nearest site when nothing nearer can be unseen
+      bool known = certified || (near != 0x7fffffff && (double)near2 <= (double)covered * (double)covered * (1.0 - 1e-5));
+      if (known && near != 0x7fffffff) {
+        if (near2 == 0.f) set_error(C.status, VD_ERR_DUPLICATE);  // coincident sites
+        delta[i] = T(0.5) * sqrt((T)near2);
+      } else if (known) {
+        delta[i] = T(1);  // no other site
+      } else {
+        T d2;
+        int k = thread_nearest(C.G, qx, qy, qz, i, d2);
+        if (k >= 0 && k < C.n && d2 == T(0)) set_error(C.status, VD_ERR_DUPLICATE);
+        delta[i] = (k >= 0 && k < C.n) ? T(0.5) * sqrt(d2) : T(1);
       }
     }
     __syncwarp();
