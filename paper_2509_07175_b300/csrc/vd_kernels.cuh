@@ -434,9 +434,8 @@ __device__ __noinline__ void knn_scan_shell(const GridView<T>& G, int lev, int c
 
 // Warp per site: collect the sites of growing rings around v_i (each lane keeps
 // the sites it meets in its own column of shared memory), then merge the lanes'
-// sorted columns into the 32 nearest (ties: smaller index).  After the first
-// ring, a radius that already holds 32 collected sites bounds the rest of the
-// scan.
+// sorted columns into the 32 nearest (ties: smaller index).  Once 32 collected
+// sites lie within some radius, that radius bounds the rest of the scan.
 // delta (optional): also writes delta_i (Sec. 5.1) from the list's first entry when
 // the scan certifies it as the nearest site, with the checks of k_delta; a site whose
 // nearest is not certified by the scan gets its own nearest-site query.
@@ -456,12 +455,15 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     T qx = s4.x, qy = s4.y, qz = s4.z;
     int cnt = 0;
     bool over = false;
+    T bound2 = T(1e36);  // squared radius already holding 32 collected sites
     auto visit = [&](const typename Prec<T>::V4& s) {
       int k = site_id(s);
       if (k == i) return;
       T dx = s.x - qx, dy = s.y - qy, dz = s.z - qz;
+      T d = dx * dx + dy * dy + dz * dz;
+      if (d > bound2) return;  // cannot be one of the 32 nearest
       if (cnt < KNN_SLOTS) {
-        S.d2[cnt][lane] = (float)(dx * dx + dy * dy + dz * dz);
+        S.d2[cnt][lane] = (float)d;
         S.id[cnt][lane] = k;
         ++cnt;
       } else {
@@ -479,7 +481,6 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     // the stored distances are below cover^2 (so no unseen site can be nearer
     // than the 32nd); otherwise the list is kept for the features but flagged
     bool certified = false;
-    T bound2 = T(1e36);  // squared radius holding 32 collected sites (after ring 1)
     T covered = T(0);    // every site within this distance of v_i has been collected
     for (int r = 1;; ++r) {
       knn_scan_shell(C.G, lev, cx, cy, cz, r, lane, S.ss, visit, qx, qy, qz, bound2);
@@ -492,17 +493,17 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
       if (total >= KNN) {
         float m2 = (float)(m * m) * (1.f - 1e-5f);
         if (count_below(m2) >= KNN) { certified = true; break; }
-        if (r == 1) {
-          // a radius with 32 collected sites within it: the largest of each lane's
-          // distances bounds its column, so grow a guess from the cover until the
-          // count reaches 32 (at worst the largest collected distance)
-          float top = 0.f;
-          for (int t = 0; t < cnt; ++t) top = fmaxf(top, S.d2[t][lane]);
-          top = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(top)));
-          float g = m2 > 0.f ? m2 : top;
-          while (g < top && count_below(g) < KNN) g = fminf(top, 2.f * g);
-          bound2 = (T)g * T(1.0001);
-        }
+        // a radius with 32 collected sites within it bounds the rest of the scan
+        // (cells beyond it are skipped, sites beyond it are not stored): grow a
+        // guess from the cover until the count reaches 32 (at worst the largest
+        // collected distance)
+        float top = 0.f;
+        for (int t = 0; t < cnt; ++t) top = fmaxf(top, S.d2[t][lane]);
+        top = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(top)));
+        float g = m2 > 0.f ? m2 : top;
+        while (g < top && count_below(g) < KNN) g = fminf(top, 2.f * g);
+        T nb = (T)g * T(1.0001);
+        bound2 = nb < bound2 ? nb : bound2;
       }
       if (r >= 4) break;
     }
