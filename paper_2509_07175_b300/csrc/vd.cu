@@ -62,6 +62,7 @@ struct vd_ctx {
   void* lgs[MAX_LEVELS] = {};         // hashed levels: sorted sites
   long long lbuckets[MAX_LEVELS] = {};
   unsigned char* qlev = nullptr;      // [G] query level of each level-0 cell
+  unsigned char* qlev_nbr = nullptr;  // [G] the same for the densest cell around it (split's boundary pass)
   void* gs = nullptr;
   void* delta = nullptr;
   unsigned long long *hash = nullptr, *queue = nullptr, *ctr = nullptr;
@@ -176,6 +177,7 @@ static void free_domain(vd_ctx* c) {
   c->have_domain = false;
   c->split_ok = false;
   c->bsimp = c->badj = c->btet = c->bnd = nullptr;
+  c->qlev_nbr = nullptr;
   c->computed = false;
   c->sites_fresh = c->knn_fresh = false;
   c->tuned = false;
@@ -282,7 +284,8 @@ static void enqueue_compute(vd_ctx* c) {
     k_cell_scatter<T><<<bn, 256, 0, s>>>(D, c->cellid, start, c->ccur, (typename Prec<T>::V4*)gs);
     c->launches += 2 + scan_launches(nb + 1);
     if (l == 0 && c->nlev > 1) {
-      k_query_level<<<nblk(c->G, 256), 256, 0, s>>>((int)c->G, c->cstart, c->qlev, c->nlev, c->rho);
+      k_query_level<<<nblk(c->G, 256), 256, 0, s>>>(c->gx, c->gy, c->gz, c->cstart, c->qlev,
+                                                    split_active(c) ? c->qlev_nbr : nullptr, c->nlev, c->rho);
       c->launches += 1;
     }
   }
@@ -316,6 +319,7 @@ static void enqueue_compute(vd_ctx* c) {
       Dev<float> S = D;
       S.mode = VD_MODE_SURFACE; S.m = (int)c->mb; S.k = 3; S.simp = c->bsimp; S.adj = c->badj;
       S.fsgn = nullptr; S.tsgn = nullptr; S.want_stats = 0; S.split = 0; S.box = 0;
+      if (c->nlev > 1) S.G.qlev = c->qlev_nbr;  // boundary points: level of the densest neighbour
       unsigned pg = (unsigned)std::max(1, c->nsm * 8);
       unsigned long long* seeds = (unsigned long long*)c->pm1;  // free until the 3D flood writes it
       cudaMemsetAsync(c->bnd, 0, sizeof(int) * c->n, s);
@@ -859,6 +863,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
     c->lgs[l] = p;
   }
   DALLOC(c->qlev, unsigned char, c->G, true);
+  if (c->split_ok) DALLOC(c->qlev_nbr, unsigned char, c->G, true);
   DALLOC(c->knn, int, n * KNN, true);
   DALLOC(c->knn_d2, float, n * KNN, true);
   DALLOC(c->cmask, unsigned, n, true);

@@ -95,14 +95,33 @@ __global__ void k_cell_scatter(Dev<T> C, const int* cellid, const int* cstart, i
 }
 
 // query level of every level-0 cell: the level whose cells hold about rho sites
-// at the cell's own density (each level halves the cell edge)
-__global__ void k_query_level(int G0, const int* cstart0, unsigned char* qlev, int nlev, float rho) {
+// at the cell's own density (each level halves the cell edge).  qlev_nbr: the
+// same for the densest cell of the 3x3x3 block around it, for queries that lie
+// mostly off the sites (the boundary pass of the split queries points on the
+// domain's boundary, where a sparse cell can border a dense cluster whose sites
+// its level-0 ring would scan one by one).
+__global__ void k_query_level(int gx, int gy, int gz, const int* cstart0, unsigned char* qlev,
+                              unsigned char* qlev_nbr, int nlev, float rho) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= G0) return;
-  float cnt = (float)(cstart0[c + 1] - cstart0[c]);
-  int l = 0;
-  if (cnt > rho) l = (int)ceilf(log2f(cnt / rho) / 3.f - 0.15f);
-  qlev[c] = (unsigned char)min(l, nlev - 1);
+  if (c >= gx * gy * gz) return;
+  auto level = [&](int cnt) {
+    int l = 0;
+    if ((float)cnt > rho) l = (int)ceilf(log2f((float)cnt / rho) / 3.f - 0.15f);
+    return (unsigned char)min(l, nlev - 1);
+  };
+  qlev[c] = level(cstart0[c + 1] - cstart0[c]);
+  if (qlev_nbr) {
+    int x = c % gx, y = (c / gx) % gy, z = c / (gx * gy), mx = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int xx = x + dx, yy = y + dy, zz = z + dz;
+          if (xx < 0 || yy < 0 || zz < 0 || xx >= gx || yy >= gy || zz >= gz) continue;
+          int cc = (zz * gy + yy) * gx + xx;
+          mx = max(mx, cstart0[cc + 1] - cstart0[cc]);
+        }
+    qlev_nbr[c] = level(mx);
+  }
 }
 
 // delta_i = half the distance from v_i to its nearest other site (Sec. 5.1)
