@@ -73,6 +73,29 @@ def test_split_against_oracle(gpu, case, n, seed):
         assert st["whole_cells"] + st["boundary_sites"] <= n
 
 
+def test_split_sites_on_tetrahedron_faces(gpu):
+    """Sites exactly on faces of the tetrahedra -- the cube faces x = 0.5 shared by
+    two cells of the lattice, the diagonal faces x = y inside a cell, the domain
+    boundary x = 0 -- and on the central mesh vertex: no tetrahedron holds them
+    strictly, so they are computed per tetrahedron from every tetrahedron that
+    may hold them.  Random coordinates in the face keep the configuration free of
+    exact ties (symmetric sites would tie in Eq. 1 in any form)."""
+    v, s = I.kuhn_lattice_tets(2)
+    rng = np.random.default_rng(69)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    b, c = f32(rng.uniform(0.0, 1.0, (2, 80)))
+    on_mid = np.stack([np.full(80, 0.5), b, c], 1)
+    a, z = f32(rng.uniform(0.0, 0.5, (2, 80)))
+    on_diag = np.stack([a, a, z], 1)
+    b, c = f32(rng.uniform(0.0, 1.0, (2, 40)))
+    on_bnd = np.stack([np.zeros(40), b, c], 1)
+    sites = np.concatenate([on_mid, on_diag, on_bnd, [[0.5, 0.5, 0.5]], f32(rng.uniform(0.0, 1.0, (500, 3)))])
+    sites = np.unique(sites, axis=0)
+    st = _check(_w(sites, v, s))
+    # at most the 500 random sites and none of those on a face can be whole cells
+    assert 0 < st["whole_cells"] <= 500
+
+
 def test_split_sites_outside_the_domain(gpu):
     """Sites over twice the cube's extent: cells reaching in from outside are
     boundary sites, cells missing the cube are empty with no pair at all."""
