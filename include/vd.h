@@ -210,11 +210,12 @@ int vd_compute(vd_ctx* ctx, vd_result* out);
 
 /* Autotune the clip kernel now on the current sites (batching, Sec. 4.3: one
  * persistent launch drains the pair queue): runs vd_compute's work once per
- * candidate -- one warp or one thread per pair (3D FP32), queue chunk 1 or 4
- * (or vd_options.chunk when set) -- times the clip phase with CUDA events and
- * caches the fastest for mapping 0.  mapping, chunk (may be NULL) receive the
- * choice; times_ms (host float[8], may be NULL) the candidates' times in the
- * order (warp,1), (warp,4), (thread,1), (thread,4), -1 for those not run.  All
+ * candidate -- one warp or one thread per pair (3D FP32 tetrahedra without the
+ * split), queue chunk 1, 2, 4, 8 or 16 (or vd_options.chunk alone when set) --
+ * times the clip phase with CUDA events and caches the fastest for mapping 0.
+ * mapping, chunk (may be NULL) receive the choice; times_ms (host float[10],
+ * may be NULL) the candidates' times in the order (warp,1), (warp,2), (warp,4),
+ * (warp,8), (warp,16), (thread,1), ..., (thread,16), -1 for those not run.  All
  * candidates compute the same diagram; the result of the last one is left as
  * the current result.  Synchronises the context stream. */
 int vd_autotune(vd_ctx* ctx, int* mapping, int* chunk, float* times_ms);

@@ -308,9 +308,9 @@ class Diagram:
     def autotune(self):
         """Time every clip-kernel mapping on the current sites; returns the choice and the times."""
         m, ch = ctypes.c_int(), ctypes.c_int()
-        times = (ctypes.c_float * 8)()
+        times = (ctypes.c_float * 10)()
         _check(load().vd_autotune(self._h, ctypes.byref(m), ctypes.byref(ch), times), "vd_autotune")
-        names = ("warp,1", "warp,4", "thread,1", "thread,4")
+        names = tuple(f"{mp},{k}" for mp in ("warp", "thread") for k in (1, 2, 4, 8, 16))
         return {"mapping": m.value, "chunk": ch.value,
                 "times_ms": {nm: float(t) for nm, t in zip(names, times) if t >= 0}}
 

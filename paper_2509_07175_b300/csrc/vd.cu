@@ -29,6 +29,8 @@ struct Buf {
 };
 
 constexpr int MLP_RANK_BLOCKS = 3;    // inference blocks per SM (61 KB of shared memory each)
+constexpr int TUNE_CHUNKS = 5;        // queue chunks the autotuner tries per mapping
+constexpr int kTuneChunks[TUNE_CHUNKS] = {1, 2, 4, 8, 16};
 constexpr int MLP_MAX_EPOCHS = 1024;  // per-epoch loss slots of vd_mlp_train
 
 }  // namespace
@@ -99,7 +101,7 @@ struct vd_ctx {
   int cur_mapping = 1, cur_chunk = 1;  // used by the next enqueue
   bool tuned = false;             // autotuned choice cached for the current domain and options
   int tuned_mapping = 1, tuned_chunk = 1;
-  float tune_ms[8] = {0};         // clip-phase time of each candidate of the last autotune
+  float tune_ms[2 * TUNE_CHUNKS] = {0};  // clip-phase time of each candidate of the last autotune
   bool have_domain = false;
   bool box = false;               // box domain (vd_set_box)
   float blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
@@ -923,18 +925,27 @@ static bool wants_network(const vd_ctx* c) {
 // clip phase with CUDA events on the context stream and caches the fastest for
 // the current domain and options.  Every candidate produces the same diagram.
 static int autotune(vd_ctx* c) {
-  int cand_m[8], cand_c[8], nc = 0;
-  const int chunks[2] = {1, 4};
+  // candidates: mapping (1 warp, 2 thread per pair) x queue chunk; slot of each
+  // in tune_ms: (mapping - 1) * TUNE_CHUNKS + index of the chunk
+  int cand_m[2 * TUNE_CHUNKS], cand_c[2 * TUNE_CHUNKS], cand_s[2 * TUNE_CHUNKS], nc = 0;
   for (int m = 1; m <= 2; ++m) {
     if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c))) continue;
-    if (c->opt.chunk > 0) { cand_m[nc] = m; cand_c[nc++] = std::min(c->opt.chunk, 64); continue; }
-    for (int k = 0; k < 2; ++k) { cand_m[nc] = m; cand_c[nc++] = chunks[k]; }
+    for (int k = 0; k < TUNE_CHUNKS; ++k) {
+      int ch = c->opt.chunk > 0 ? std::min(c->opt.chunk, 64) : kTuneChunks[k];
+      cand_m[nc] = m; cand_c[nc] = ch; cand_s[nc++] = (m - 1) * TUNE_CHUNKS + k;
+      if (c->opt.chunk > 0) {  // the caller's chunk: one candidate per mapping, in its slot if listed
+        cand_s[nc - 1] = -1;
+        for (int q = 0; q < TUNE_CHUNKS; ++q)
+          if (kTuneChunks[q] == ch) cand_s[nc - 1] = (m - 1) * TUNE_CHUNKS + q;
+        break;
+      }
+    }
   }
   if (!c->ev[0])
     for (int k = 0; k <= VD_PHASE_N; ++k) CK(cudaEventCreate(&c->ev[k]));
   int best = 0;
   double best_ms = 1e300;
-  for (int k = 0; k < 8; ++k) c->tune_ms[k] = -1.f;
+  for (int k = 0; k < 2 * TUNE_CHUNKS; ++k) c->tune_ms[k] = -1.f;
   for (int k = 0; k < nc; ++k) {
     c->cur_mapping = cand_m[k];
     c->cur_chunk = cand_c[k];
@@ -947,7 +958,7 @@ static int autotune(vd_ctx* c) {
     if (e != cudaSuccess) return VD_ERR_CUDA;
     if (st) return st;
     double ms = c->last_phase_ms[VD_PHASE_CLIP];
-    c->tune_ms[k] = (float)ms;
+    if (cand_s[k] >= 0) c->tune_ms[cand_s[k]] = (float)ms;
     if (ms < best_ms) { best_ms = ms; best = k; }
   }
   c->sites_fresh = true;

@@ -89,7 +89,7 @@ def test_autotune_choice_and_cache(gpu):
     ref = d.compute()
     d.set_options(mapping=0, stats=1)
     t = d.autotune()
-    assert set(t["times_ms"]) == {"warp,1", "warp,4", "thread,1", "thread,4"}
+    assert set(t["times_ms"]) == {f"{mp},{k}" for mp in ("warp", "thread") for k in (1, 2, 4, 8, 16)}
     assert all(v > 0 for v in t["times_ms"].values())
     best = min(t["times_ms"], key=t["times_ms"].get)
     assert best == f"{'warp' if t['mapping'] == 1 else 'thread'},{t['chunk']}"
@@ -112,5 +112,5 @@ def test_polygon_modes_fall_back_to_warp(gpu):
         _same(ref, r, name)
         d.set_options(mapping=0)
         t = d.autotune()
-        assert set(t["times_ms"]) == {"warp,1", "warp,4"}
+        assert set(t["times_ms"]) == {f"warp,{k}" for k in (1, 2, 4, 8, 16)}
         d.close()
