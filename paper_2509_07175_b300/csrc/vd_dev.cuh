@@ -261,13 +261,14 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
     *wit = -1;
     return 0;
   }
-  // learned proposal, outside certificate: a ranked candidate certified closer than
-  // v_i settles "outside" with no grid scan (same exact criterion as the scan)
-  if (__any_sync(FULL, L.cand)) {
+  // learned proposal, outside certificate: a listed site (a ranked candidate or
+  // one of the other nearest sites) certified closer than v_i settles "outside"
+  // with no grid scan (same exact criterion as the scan)
+  if (__any_sync(FULL, L.id >= 0)) {
     T cd = T(1e30);
     int ck = 0x7fffffff;
     int k = L.id;
-    if (L.cand && k != i && k != e0 && k != e1 && k != e2) {
+    if (k >= 0 && k != i && k != e0 && k != e1 && k != e2) {
       T dx = L.x - gx, dy = L.y - gy, dz = L.z - gz;
       T d2 = dx * dx + dy * dy + dz * dz;
       if (d2 - di2 < -B) { cd = d2; ck = k; }
