@@ -86,6 +86,8 @@ struct vd_ctx {
   int ncand = 0;
   int* knn = nullptr;             // [n*32] nearest sites (learned proposal)
   float* knn_d2 = nullptr;
+  int* knn2 = nullptr;            // [n*32] the 33rd..64th nearest
+  float* knn_r64 = nullptr;       // [n] certified radius of the 64 nearest
   unsigned* cmask = nullptr;      // [n] ranked candidates among the 32 nearest
   bool knn_fresh = false;         // knn holds the lists of the last compute's sites
   bool sites_fresh = false;       // sites unchanged since the last compute
@@ -216,6 +218,8 @@ static Dev<T> make_dev(vd_ctx* c) {
   else { D.cand = nullptr; D.ncand = 0; }
   D.knn = (c->opt.learned && !c->cand) ? c->knn : nullptr;
   D.knn_d2 = c->knn_d2;
+  D.knn2 = D.knn ? c->knn2 : nullptr;
+  D.knn_r64 = c->knn_r64;
   D.cmask = c->cmask;
   D.hash = c->hash; D.hmask = c->hmask; D.queue = c->queue; D.qcap = c->qcap; D.ctr = c->ctr;
   D.pmeas = (T*)c->pmeas; D.pm1 = (T*)c->pm1; D.pfoff = c->pfoff; D.pfcnt = c->pfcnt; D.pflags = c->pflags;
@@ -300,7 +304,8 @@ static void enqueue_compute(vd_ctx* c) {
   }
   if (c->opt.learned && !c->cand) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
-    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, fused ? (T*)c->delta : nullptr);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, fused ? (T*)c->delta : nullptr,
+                                                     c->knn2, c->knn_r64);
     if (c->opt.proposal == VD_PROPOSAL_MLP)
       mlp::k_mlp_rank<T><<<c->nsm * MLP_RANK_BLOCKS, 128, sizeof(mlp::RankSmem), s>>>(
           D, c->knn, (const T*)c->delta, c->mlp_wb, c->mlp_p, c->opt.topk, c->cmask);
@@ -868,6 +873,8 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
   if (c->split_ok) DALLOC(c->qlev_nbr, unsigned char, c->G, true);
   DALLOC(c->knn, int, n * KNN, true);
   DALLOC(c->knn_d2, float, n * KNN, true);
+  DALLOC(c->knn2, int, n * KNN, true);
+  DALLOC(c->knn_r64, float, n, true);
   DALLOC(c->cmask, unsigned, n, true);
   DALLOC(c->cellid, int, n, true);
   DALLOC(c->ccount, int, nbmax + 1, true);
@@ -1282,7 +1289,7 @@ int mlp_features_t(vd_ctx* c, void* x, uint32_t* labels) {
   cudaStream_t s = c->stream;
   Dev<T> D = make_dev<T>(c);
   if (!c->knn_fresh) {
-    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, nullptr);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, nullptr, c->knn2, c->knn_r64);
     c->knn_fresh = true;
   }
   if (x)

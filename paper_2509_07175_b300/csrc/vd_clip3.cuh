@@ -274,6 +274,29 @@ __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const Nb
       K.nn++;
       return kk;
     }
+    // the 64 nearest (each lane also takes its entry among the 33rd..64th)
+    if (L.r64 > 0.f && 2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= L.r64) {
+      float d2 = 1e30f;
+      int kk = 0x7fffffff;
+      if (L.id >= 0) {
+        float dx = L.x - px, dy = L.y - py, dz = L.z - pz;
+        d2 = dx * dx + dy * dy + dz * dz;
+        kk = L.id;
+      }
+      int k2 = C.knn2[(long long)i * 32 + lane];
+      if (k2 >= 0) {
+        float dx = C.sites[3 * k2] - px, dy = C.sites[3 * k2 + 1] - py, dz = C.sites[3 * k2 + 2] - pz;
+        float e2 = dx * dx + dy * dy + dz * dz;
+        if (e2 < d2 || (e2 == d2 && k2 < kk)) { d2 = e2; kk = k2; }
+      }
+      float dxi = vi.x - px, dyi = vi.y - py, dzi = vi.z - pz;
+      float di2 = dxi * dxi + dyi * dyi + dzi * dzi;
+      if (lane == 0 && (di2 < d2 || (di2 == d2 && i < kk))) { d2 = di2; kk = i; }
+      warp_argmin(d2, kk);
+      K.list++;
+      K.nn++;
+      return kk;
+    }
   }
   return nn_query(C, W, px, py, pz, lane, K);
 }

@@ -218,6 +218,30 @@ __device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const Nbr
       K.list++;
       return kk;
     }
+    // the 64 nearest (each lane also takes its entry among the 33rd..64th)
+    if (L.r64 > 0.f &&
+        (float)(T(2) * s) * (1.f + 2e-5f) + 4e-7f * (float)(fabs(px) + fabs(py) + fabs(pz)) <= L.r64) {
+      T d2 = T(1e30);
+      int kk = 0x7fffffff;
+      if (L.id >= 0) {
+        T dx = L.x - px, dy = L.y - py, dz = L.z - pz;
+        d2 = dx * dx + dy * dy + dz * dz;
+        kk = L.id;
+      }
+      int k2 = C.knn2[(long long)i * 32 + lane];
+      if (k2 >= 0) {
+        T dx = C.sites[3 * k2] - px, dy = C.sites[3 * k2 + 1] - py, dz = C.sites[3 * k2 + 2] - pz;
+        T e2 = dx * dx + dy * dy + dz * dz;
+        if (e2 < d2 || (e2 == d2 && k2 < kk)) { d2 = e2; kk = k2; }
+      }
+      T dxi = vi[0] - px, dyi = vi[1] - py, dzi = vi[2] - pz;
+      T di2 = dxi * dxi + dyi * dyi + dzi * dzi;
+      if (lane == 0 && (di2 < d2 || (di2 == d2 && i < kk))) { d2 = di2; kk = i; }
+      warp_argmin(d2, kk);
+      K.nn++;
+      K.list++;
+      return kk;
+    }
   }
   return nn_query(C, W, px, py, pz, lane, K);
 }

@@ -27,6 +27,8 @@ struct Dev {
   const int* knn;        // [n*32] nearest other sites, ascending (learned form), or null
   const float* knn_d2;   // [n*32] their squared distances (FP32); 32nd < 0: list not certified
   const unsigned* cmask; // [n] learned form: which of the 32 nearest are ranked candidates
+  const int* knn2;       // [n*32] the 33rd..64th nearest (any order, -1 unused), or null
+  const float* knn_r64;  // [n] certified radius of the 64 nearest (0: not certified)
   // pair set and queue
   unsigned long long* hash;
   unsigned long long hmask;
@@ -150,25 +152,28 @@ __device__ __forceinline__ void stat_add(const Dev<T>& C, int slot, unsigned lon
 // ---------------------------------------------------------------------------
 // Learned form: the 32 nearest sites of v_i, one per lane, loaded once per pair.
 // cand marks the ranked candidates; r32 (> 0) is a certified lower bound on the
-// distance from v_i to every site that is not in the list.
+// distance from v_i to every site that is not in the list.  r64 (> 0) is the
+// same for the list extended by the 33rd..64th nearest, which are loaded only
+// by the tests that need them.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct NbrList {
   int id;       // this lane's site (-1: none)
   T x, y, z;
   bool cand;
-  float r32;
+  float r32, r64;
 };
 
 template <typename T>
 __device__ __forceinline__ NbrList<T> load_nbrs(const Dev<T>& C, int i, int lane) {
   NbrList<T> L;
-  L.id = -1; L.x = L.y = L.z = T(0); L.cand = false; L.r32 = 0.f;
+  L.id = -1; L.x = L.y = L.z = T(0); L.cand = false; L.r32 = 0.f; L.r64 = 0.f;
   if (C.knn) {
     L.id = C.knn[(long long)i * 32 + lane];
     float d32 = C.knn_d2[(long long)i * 32 + 31];
     int k32 = C.knn[(long long)i * 32 + 31];
     L.r32 = (d32 > 0.f && k32 >= 0) ? sqrtf(d32 * (1.f - 1e-6f)) : 0.f;
+    if (C.knn2 && L.r32 > 0.f) L.r64 = C.knn_r64[i];
     L.cand = L.id >= 0 && ((C.cmask[i] >> lane) & 1u);
   } else if (C.ncand > 0) {
     L.id = lane < C.ncand ? C.cand[(long long)i * C.ncand + lane] : -1;
@@ -248,6 +253,39 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
       if (f < -B) { ld = d2; lk = k; }
       else if (f <= B && exact(k) < 0) { lo = d2; lok = k; }
     }
+    if (__any_sync(FULL, lk != 0x7fffffff)) {
+      warp_argmin(ld, lk);
+      *wit = lk;
+      return 1;
+    }
+    if (__any_sync(FULL, lok != 0x7fffffff)) {
+      warp_argmin(lo, lok);
+      *wit = lok;
+      return 1;
+    }
+    *wit = -1;
+    return 0;
+  }
+  // the same with the 64 nearest, when their radius covers the ball: each lane
+  // also tests its entry among the 33rd..64th (loaded here, rarely needed)
+  if (L.r64 > 0.f && L.r64 >= 2.f * (float)(di + delta) * (1.f + 2e-5f)) {
+    *listed += 1;
+    T ld = T(1e30), lo = T(1e30);
+    int lk = 0x7fffffff, lok = 0x7fffffff;
+    auto test = [&](int k, T x, T y, T z) {
+      if (k < 0 || k == e0 || k == e1 || k == e2) return;
+      T dx = x - gx, dy = y - gy, dz = z - gz;
+      T d2 = dx * dx + dy * dy + dz * dz;
+      T f = d2 - di2;
+      if (f < -B) {
+        if (d2 < ld || (d2 == ld && k < lk)) { ld = d2; lk = k; }
+      } else if (f <= B && (d2 < lo || (d2 == lo && k < lok)) && exact(k) < 0) {
+        lo = d2; lok = k;
+      }
+    };
+    test(L.id, L.x, L.y, L.z);
+    int k2 = C.knn2[(long long)i * 32 + lane];
+    if (k2 >= 0) test(k2, C.sites[3 * k2], C.sites[3 * k2 + 1], C.sites[3 * k2 + 2]);
     if (__any_sync(FULL, lk != 0x7fffffff)) {
       warp_argmin(ld, lk);
       *wit = lk;

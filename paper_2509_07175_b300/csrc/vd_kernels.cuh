@@ -458,9 +458,12 @@ __device__ __noinline__ void knn_scan_shell(const GridView<T>& G, int lev, int c
 // delta (optional): also writes delta_i (Sec. 5.1) from the list's first entry when
 // the scan certifies it as the nearest site, with the checks of k_delta; a site whose
 // nearest is not certified by the scan gets its own nearest-site query.
+// knn2, r64 (optional): the 33rd..64th nearest (ids) and the certified radius of
+// the 64 (0 when the scan does not certify them).
 template <typename T>
 __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ Dev<T> C, int* knn, float* knn_d2,
-                                                        T* delta) {
+                                                        T* delta, int* knn2, float* r64) {
+  const int want = knn2 ? 2 * KNN : KNN;
   __shared__ KnnScratch sh[KNN_WARPS];
   KnnScratch& S = sh[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     // certified: every site within `cover` of v_i was stored and at least 32 of
     // the stored distances are below cover^2 (so no unseen site can be nearer
     // than the 32nd); otherwise the list is kept for the features but flagged
-    bool certified = false;
+    bool certified = false, certified2 = false;
     T covered = T(0);    // every site within this distance of v_i has been collected
     for (int r = 1;; ++r) {
       knn_scan_shell(C.G, lev, cx, cy, cz, r, lane, S.ss, visit, qx, qy, qz, bound2);
@@ -507,28 +510,31 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
       if (__any_sync(FULL, over)) break;
       T m = C.G.cover(lev, cx, cy, cz, r, qx, qy, qz);
       covered = r == 1 || bound2 > m * m ? m : sqrt(bound2);
-      if (m >= T(1e29)) { certified = true; break; }
+      if (m >= T(1e29)) { certified = certified2 = true; break; }
       int total = (int)__reduce_add_sync(FULL, (unsigned)cnt);
       if (total >= KNN) {
         float m2 = (float)(m * m) * (1.f - 1e-5f);
-        if (count_below(m2) >= KNN) { certified = true; break; }
-        // a radius with 32 collected sites within it bounds the rest of the scan
-        // (cells beyond it are skipped, sites beyond it are not stored): grow a
-        // guess from the cover until the count reaches 32 (at worst the largest
+        int below = count_below(m2);
+        if (below >= KNN) certified = true;  // the first 32 stay certified: later rings lie beyond m
+        if (below >= want) { certified2 = true; break; }
+        // a radius with `want` collected sites within it bounds the rest of the
+        // scan (cells beyond it are skipped, sites beyond it are not stored): grow
+        // a guess from the cover until the count reaches it (at worst the largest
         // collected distance)
+        if (total < want) { if (r >= 4) break; continue; }
         float top = 0.f;
         for (int t = 0; t < cnt; ++t) top = fmaxf(top, S.d2[t][lane]);
         top = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(top)));
         float g = m2 > 0.f ? m2 : top;
-        while (g < top && count_below(g) < KNN) g = fminf(top, 2.f * g);
+        while (g < top && count_below(g) < want) g = fminf(top, 2.f * g);
         T nb = (T)g * T(1.0001);
         bound2 = nb < bound2 ? nb : bound2;
       }
       if (r >= 4) break;
     }
     __syncwarp();
-    // each lane sorts its column (insertion sort; ties by index), then 32 rounds
-    // of a warp-wide minimum over the column heads
+    // each lane sorts its column (insertion sort; ties by index), then one round
+    // of a warp-wide minimum over the column heads per output entry
     for (int u = 1; u < cnt; ++u) {
       float du = S.d2[u][lane];
       int iu = S.id[u][lane];
@@ -544,7 +550,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     int head = 0;
     float near2 = 3.0e38f;
     int near = 0x7fffffff;
-    for (int k = 0; k < KNN; ++k) {
+    // entry k is kept by lane k % 32 and written with the others of its half
+    int mine = -1;
+    float mined = 0.f;
+    for (int k = 0; k < want; ++k) {
       float bd = head < cnt ? S.d2[head][lane] : 3.0e38f;
       int bi = head < cnt ? S.id[head][lane] : 0x7fffffff;
       float d0 = bd;
@@ -552,10 +561,14 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
       warp_argmin(bd, bi);
       if (d0 == bd && i0 == bi && head < cnt) ++head;
       if (k == 0) { near2 = bd; near = bi; }
-      if (lane == 0) {
-        knn[(long long)i * KNN + k] = bi == 0x7fffffff ? -1 : bi;
+      if (lane == (k & (KNN - 1))) { mine = bi == 0x7fffffff ? -1 : bi; mined = bd; }
+      if (k == KNN - 1) {
+        knn[(long long)i * KNN + lane] = mine;
         // a negative 32nd distance marks a list that is not certified complete
-        knn_d2[(long long)i * KNN + k] = (k == KNN - 1 && !certified) ? -1.f : bd;
+        knn_d2[(long long)i * KNN + lane] = (lane == KNN - 1 && !certified) ? -1.f : mined;
+      } else if (k == 2 * KNN - 1) {
+        knn2[(long long)i * KNN + lane] = mine;
+        if (lane == KNN - 1) r64[i] = (certified2 && mine >= 0) ? sqrtf(mined * (1.f - 1e-6f)) : 0.f;
       }
     }
     if (delta && lane == 0) {
