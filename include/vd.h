@@ -83,7 +83,8 @@ enum {
   VD_STAT_BOUNDARY_SITES = 25,/* split = 1: sites whose cell meets the boundary surface (always) */
   VD_STAT_LIST_TESTS = 30,    /* point-in-cell tests and queries settled from the 32 nearest
                                  sites of the cell's site, with no grid scan (learned form) */
-  VD_STAT_MAPPING = 31,       /* clip-kernel mapping used: mapping | chunk << 8 (always) */
+  VD_STAT_MAPPING = 31,       /* clip-kernel mapping used: mapping | chunk << 8 | list << 16
+                                 (list: 64 or 32 sites per learned list) (always) */
   VD_STAT_N = 32
 };
 
@@ -121,6 +122,11 @@ typedef struct {
                               centroids and neighbours are those of split = 0 (the same cells,
                               summed in fewer pieces); ignored in other modes and by vd_set_box.
                               Clip kernel: one warp per pair. */
+  int nearest;             /* learned form (32-NN lists): 64 also stores the 33rd..64th nearest
+                              and settles point-in-cell tests and searches out to half their
+                              radius from the lists (fewer grid scans, a costlier list pass);
+                              32 the 32 only; 0 chosen by the autotuner with mapping 0 (64
+                              until tuned). */
 } vd_options;
 
 enum { VD_PROPOSAL_DISTANCE = 0, VD_PROPOSAL_MLP = 1 };
@@ -213,9 +219,13 @@ int vd_compute(vd_ctx* ctx, vd_result* out);
  * candidate -- one warp or one thread per pair (3D FP32 tetrahedra without the
  * split), queue chunk 1, 2, 4, 8 or 16 (or vd_options.chunk alone when set) --
  * times the clip phase with CUDA events and caches the fastest for mapping 0.
- * mapping, chunk (may be NULL) receive the choice; times_ms (host float[10],
- * may be NULL) the candidates' times in the order (warp,1), (warp,2), (warp,4),
- * (warp,8), (warp,16), (thread,1), ..., (thread,16), -1 for those not run.  All
+ * In the learned form with vd_options.nearest = 0 it first compares lists of
+ * the 32 and of the 64 nearest (warp per pair, chunk 1) on the time of the
+ * list pass, the seeding and the clip, and keeps the faster for the mapping
+ * candidates.  mapping, chunk (may be NULL) receive the choice; times_ms (host
+ * float[12], may be NULL) the candidates' clip times in the order (warp,1),
+ * (warp,2), (warp,4), (warp,8), (warp,16), (thread,1), ..., (thread,16), then
+ * the list comparison (32, 64), -1 for those not run.  All
  * candidates compute the same diagram; the result of the last one is left as
  * the current result.  Synchronises the context stream. */
 int vd_autotune(vd_ctx* ctx, int* mapping, int* chunk, float* times_ms);

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("stats", ctypes.c_int), ("queue_capacity", ctypes.c_int64), ("max_clips", ctypes.c_int),
                 ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
                 ("timing", ctypes.c_int), ("grid_density", ctypes.c_double), ("topk", ctypes.c_int),
-                ("proposal", ctypes.c_int), ("split", ctypes.c_int)]
+                ("proposal", ctypes.c_int), ("split", ctypes.c_int),
+                ("nearest", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -225,7 +226,7 @@ class Diagram:
                           error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]],
                           list_tests=int(r.stats[30]), whole_cells=int(r.stats[24]),
                           boundary_sites=int(r.stats[25]), mapping=int(r.stats[31]) & 255,
-                          chunk=int(r.stats[31]) >> 8),
+                          chunk=(int(r.stats[31]) >> 8) & 255, nearest=int(r.stats[31]) >> 16),
             "phase_ms": dict(zip(PHASE_NAMES, [float(x) for x in r.phase_ms][:len(PHASE_NAMES)])),
         }
         return out
@@ -308,9 +309,9 @@ class Diagram:
     def autotune(self):
         """Time every clip-kernel mapping on the current sites; returns the choice and the times."""
         m, ch = ctypes.c_int(), ctypes.c_int()
-        times = (ctypes.c_float * 10)()
+        times = (ctypes.c_float * 12)()
         _check(load().vd_autotune(self._h, ctypes.byref(m), ctypes.byref(ch), times), "vd_autotune")
-        names = tuple(f"{mp},{k}" for mp in ("warp", "thread") for k in (1, 2, 4, 8, 16))
+        names = tuple(f"{mp},{k}" for mp in ("warp", "thread") for k in (1, 2, 4, 8, 16)) + ("list32", "list64")
         return {"mapping": m.value, "chunk": ch.value,
                 "times_ms": {nm: float(t) for nm, t in zip(names, times) if t >= 0}}
 

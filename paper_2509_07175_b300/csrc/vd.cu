@@ -101,9 +101,13 @@ struct vd_ctx {
   int flood_grid_t = 0;           // thread-per-pair kernel (3D FP32)
   int knn_grid = 0;               // resident blocks of k_knn on the device
   int cur_mapping = 1, cur_chunk = 1;  // used by the next enqueue
+  bool cur_list64 = true;         // learned form: the 64-site lists (next enqueue)
   bool tuned = false;             // autotuned choice cached for the current domain and options
   int tuned_mapping = 1, tuned_chunk = 1;
-  float tune_ms[2 * TUNE_CHUNKS] = {0};  // clip-phase time of each candidate of the last autotune
+  bool tuned_list64 = true;
+  float tune_list_ms[2] = {-1.f, -1.f};  // delta + seed + clip with 32 / 64-site lists
+  float tune_ms[2 * TUNE_CHUNKS + 2] = {0};  // clip-phase time of each candidate of the last autotune,
+                                            // then the list comparison (tune_list_ms)
   bool have_domain = false;
   bool box = false;               // box domain (vd_set_box)
   float blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
@@ -218,7 +222,7 @@ static Dev<T> make_dev(vd_ctx* c) {
   else { D.cand = nullptr; D.ncand = 0; }
   D.knn = (c->opt.learned && !c->cand) ? c->knn : nullptr;
   D.knn_d2 = c->knn_d2;
-  D.knn2 = D.knn ? c->knn2 : nullptr;
+  D.knn2 = (D.knn && c->cur_list64) ? c->knn2 : nullptr;
   D.knn_r64 = c->knn_r64;
   D.cmask = c->cmask;
   D.hash = c->hash; D.hmask = c->hmask; D.queue = c->queue; D.qcap = c->qcap; D.ctr = c->ctr;
@@ -305,7 +309,7 @@ static void enqueue_compute(vd_ctx* c) {
   if (c->opt.learned && !c->cand) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
     k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, fused ? (T*)c->delta : nullptr,
-                                                     c->knn2, c->knn_r64);
+                                                     c->cur_list64 ? c->knn2 : nullptr, c->knn_r64);
     if (c->opt.proposal == VD_PROPOSAL_MLP)
       mlp::k_mlp_rank<T><<<c->nsm * MLP_RANK_BLOCKS, 128, sizeof(mlp::RankSmem), s>>>(
           D, c->knn, (const T*)c->delta, c->mlp_wb, c->mlp_p, c->opt.topk, c->cmask);
@@ -331,7 +335,10 @@ static void enqueue_compute(vd_ctx* c) {
       unsigned long long* seeds = (unsigned long long*)c->pm1;  // free until the 3D flood writes it
       cudaMemsetAsync(c->bnd, 0, sizeof(int) * c->n, s);
       k_seed_simplex<float><<<nblk(c->mb, 128), 128, 0, s>>>(S);
-      k_flood<float, VD_MODE_SURFACE><<<c->flood_grid_s, FLOOD_WARPS * 32, c->flood_smem_s, s>>>(S, 1);
+      if (S.knn2)
+        k_flood<float, VD_MODE_SURFACE, true><<<c->flood_grid_s, FLOOD_WARPS * 32, c->flood_smem_s, s>>>(S, 1);
+      else
+        k_flood<float, VD_MODE_SURFACE><<<c->flood_grid_s, FLOOD_WARPS * 32, c->flood_smem_s, s>>>(S, 1);
       k_split_mark<<<pg, 256, 0, s>>>(S, c->btet, c->bnd, seeds);
       cudaMemsetAsync(c->hash, 0xFF, sizeof(unsigned long long) * (c->hmask + 1), s);
       cudaMemsetAsync(c->queue, 0xFF, sizeof(unsigned long long) * c->qcap, s);
@@ -354,7 +361,10 @@ static void enqueue_compute(vd_ctx* c) {
     if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value)
       k_flood_thread<<<c->flood_grid_t, FLOOD_T_THREADS, 0, s>>>(D, c->cur_chunk);
   } else {
-    k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+    if (D.knn2)
+      k_flood<T, MODE, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+    else
+      k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
   }
   c->launches += 1;
   mark(c, 4);
@@ -403,8 +413,12 @@ static int flood_config(vd_ctx* c) {
   using W = typename WarpOf<T, MODE>::type;
   c->flood_smem = sizeof(W) * FLOOD_WARPS;
   CK(cudaFuncSetAttribute(k_flood<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->flood_smem));
-  int per_sm = 0;
+  CK(cudaFuncSetAttribute(k_flood<T, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->flood_smem));
+  int per_sm = 0, per_sm_x = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood<T, MODE>, FLOOD_WARPS * 32, c->flood_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_flood<T, MODE, true>, FLOOD_WARPS * 32,
+                                                   c->flood_smem));
+  per_sm = std::min(per_sm, per_sm_x);
   c->flood_grid = std::max(1, per_sm) * c->nsm;
   int per_sm_k = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_k, k_knn<T>, KNN_WARPS * 32, 0));
@@ -420,12 +434,23 @@ static int flood_config(vd_ctx* c) {
     c->flood_smem_s = sizeof(WS) * FLOOD_WARPS;
     CK(cudaFuncSetAttribute(k_flood<float, VD_MODE_SURFACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)c->flood_smem_s));
+    CK(cudaFuncSetAttribute(k_flood<float, VD_MODE_SURFACE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->flood_smem_s));
     int per_sm_s = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_flood<float, VD_MODE_SURFACE>, FLOOD_WARPS * 32,
                                                      c->flood_smem_s));
     c->flood_grid_s = std::max(1, per_sm_s) * c->nsm;
   }
   return VD_OK;
+}
+
+// learned form: whether the lists carry the 64 nearest (the caller's choice, else
+// the autotuned one, 64 until tuned)
+static bool list64_choice(const vd_ctx* c) {
+  if (!c->opt.learned || c->cand) return false;
+  if (c->opt.nearest == 32) return false;
+  if (c->opt.nearest == 64) return true;
+  return c->tuned ? c->tuned_list64 : true;
 }
 
 // mapping of the clip kernel for the next enqueue: the caller's choice, else the
@@ -438,6 +463,7 @@ static void resolve_mapping(vd_ctx* c) {
   }
   if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c))) m = 1;  // thread per pair: 3D FP32 tetrahedra only
   c->cur_mapping = m;
+  c->cur_list64 = list64_choice(c);
   c->cur_chunk = std::max(1, std::min(ch <= 0 ? 1 : ch, 64));
 }
 
@@ -463,7 +489,8 @@ static int read_status(vd_ctx* c) {
   c->last_status = st;
   c->computed = true;
   c->last_stats[VD_STAT_LAUNCHES] = (unsigned long long)c->launches;
-  c->last_stats[VD_STAT_MAPPING] = (unsigned long long)(c->cur_mapping | (c->cur_chunk << 8));
+  c->last_stats[VD_STAT_MAPPING] =
+      (unsigned long long)(c->cur_mapping | (c->cur_chunk << 8) | ((c->cur_list64 ? 64 : 32) << 16));
   for (int k = 0; k < VD_PHASE_N; ++k) c->last_phase_ms[k] = 0;
   if (c->timing_now) {
     const int map[5] = {VD_PHASE_GRID, VD_PHASE_DELTA, VD_PHASE_SEED, VD_PHASE_CLIP, VD_PHASE_REDUCE};
@@ -950,6 +977,29 @@ static int autotune(vd_ctx* c) {
   }
   if (!c->ev[0])
     for (int k = 0; k <= VD_PHASE_N; ++k) CK(cudaEventCreate(&c->ev[k]));
+  // learned form: lists of 32 or 64 nearest, compared on the phases they change
+  // (the list pass, the seeding and the clip) with one warp per pair, chunk 1
+  c->tune_list_ms[0] = c->tune_list_ms[1] = -1.f;
+  bool list64 = list64_choice(c);
+  if (c->opt.learned && !c->cand && c->opt.nearest == 0) {
+    for (int e = 0; e < 2; ++e) {
+      c->cur_mapping = 1;
+      c->cur_chunk = 1;
+      c->cur_list64 = e == 1;
+      CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
+      c->timing_now = true;
+      enqueue_any(c);
+      cudaError_t err = cudaGetLastError();
+      int st = read_status(c);
+      c->timing_now = false;
+      if (err != cudaSuccess) return VD_ERR_CUDA;
+      if (st) return st;
+      c->tune_list_ms[e] = (float)(c->last_phase_ms[VD_PHASE_DELTA] + c->last_phase_ms[VD_PHASE_SEED] +
+                                   c->last_phase_ms[VD_PHASE_CLIP]);
+    }
+    list64 = c->tune_list_ms[1] < c->tune_list_ms[0];
+  }
+  c->cur_list64 = list64;
   int best = 0;
   double best_ms = 1e300;
   for (int k = 0; k < 2 * TUNE_CHUNKS; ++k) c->tune_ms[k] = -1.f;
@@ -973,6 +1023,9 @@ static int autotune(vd_ctx* c) {
   c->tuned = true;
   c->tuned_mapping = cand_m[best];
   c->tuned_chunk = cand_c[best];
+  c->tuned_list64 = list64;
+  c->tune_ms[2 * TUNE_CHUNKS] = c->tune_list_ms[0];
+  c->tune_ms[2 * TUNE_CHUNKS + 1] = c->tune_list_ms[1];
   return VD_OK;
 }
 
@@ -1289,7 +1342,7 @@ int mlp_features_t(vd_ctx* c, void* x, uint32_t* labels) {
   cudaStream_t s = c->stream;
   Dev<T> D = make_dev<T>(c);
   if (!c->knn_fresh) {
-    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, nullptr, c->knn2, c->knn_r64);
+    k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, nullptr, nullptr, nullptr);
     c->knn_fresh = true;
   }
   if (x)

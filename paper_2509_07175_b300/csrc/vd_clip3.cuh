@@ -253,7 +253,8 @@ __device__ __noinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, flo
 // nearest site of the search point v_i + s.  Learned form: when 2|s| <= r32 the
 // nearest site is v_i or one of v_i's 32 nearest sites (any site at least as close
 // to the point as v_i lies within 2|s| of v_i), found with no grid scan.
-__device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const NbrList<float>& L, int i, float3 vi,
+template <typename NL>
+__device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const NL& L, int i, float3 vi,
                                          float sx, float sy, float sz, int lane, Counters& K) {
   float px = vi.x + sx, py = vi.y + sy, pz = vi.z + sz;
   if (L.r32 > 0.f) {
@@ -275,7 +276,7 @@ __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const Nb
       return kk;
     }
     // the 64 nearest (each lane also takes its entry among the 33rd..64th)
-    if (L.r64 > 0.f && 2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= L.r64) {
+    if (NL::ext && L.r64 > 0.f && 2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= L.r64) {
       float d2 = 1e30f;
       int kk = 0x7fffffff;
       if (L.id >= 0) {
@@ -303,7 +304,8 @@ __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const Nb
 
 // Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
 // Returns the bisector site j for the outside corner t.
-__device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, const NbrList<float>& L, int i, float3 vi,
+template <typename NL>
+__device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, const NL& L, int i, float3 vi,
                                           int t, int lane, Counters& K) {
   float4 q = W.tq[t];
   int wit = W.twit[t];
@@ -788,9 +790,10 @@ __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i,
 #define PROF_ADD(k) do {} while (0)
 #endif
 
+template <bool EXT>
 __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long long slot, int lane) {
   Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const NbrList<float> L = load_nbrs(C, i, lane);
+  const NbrList<float, EXT> L = load_nbrs<float, EXT>(C, i, lane);
   PROF_T0();
   float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   Masks Mk;

@@ -196,8 +196,8 @@ __device__ __noinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z
 }
 
 // nearest site of v_i + s; learned form: from the 32-NN list when 2|s| <= r32
-template <typename T>
-__device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const NbrList<T>& L, int i, const T* vi,
+template <typename T, typename NL>
+__device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const NL& L, int i, const T* vi,
                                          T sx, T sy, T sz, int lane, Counters& K) {
   T px = vi[0] + sx, py = vi[1] + sy, pz = vi[2] + sz;
   if (L.r32 > 0.f) {
@@ -219,7 +219,7 @@ __device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const Nbr
       return kk;
     }
     // the 64 nearest (each lane also takes its entry among the 33rd..64th)
-    if (L.r64 > 0.f &&
+    if (NL::ext && L.r64 > 0.f &&
         (float)(T(2) * s) * (1.f + 2e-5f) + 4e-7f * (float)(fabs(px) + fabs(py) + fabs(pz)) <= L.r64) {
       T d2 = T(1e30);
       int kk = 0x7fffffff;
@@ -246,8 +246,8 @@ __device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const Nbr
   return nn_query(C, W, px, py, pz, lane, K);
 }
 
-template <typename T>
-__device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, const NbrList<T>& L, int i, const T* vi,
+template <typename T, typename NL>
+__device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, const NL& L, int i, const T* vi,
                                           int k, int lane, Counters& K) {
   typename Prec<T>::V4 q = W.vq[k];
   int wit = W.vwit[k];
@@ -353,12 +353,12 @@ __device__ __noinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int
   return 0;
 }
 
-template <typename T>
+template <typename T, bool EXT>
 __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long long slot, int lane) {
   using V4 = typename Prec<T>::V4;
   Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T vi[3] = {C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]};
-  const NbrList<T> L = load_nbrs(C, i, lane);
+  const NbrList<T, EXT> L = load_nbrs<T, EXT>(C, i, lane);
   int np = 4, nv = 3;
   if (lane < 4) {
     V4 P;

@@ -156,24 +156,27 @@ __device__ __forceinline__ void stat_add(const Dev<T>& C, int slot, unsigned lon
 // same for the list extended by the 33rd..64th nearest, which are loaded only
 // by the tests that need them.
 // ---------------------------------------------------------------------------
-template <typename T>
+// EXT: the clip kernel is compiled with the 64-site tests (a separate
+// instantiation, so that workloads that do not need them keep the lean code).
+template <typename T, bool EXT = false>
 struct NbrList {
+  static constexpr bool ext = EXT;
   int id;       // this lane's site (-1: none)
   T x, y, z;
   bool cand;
   float r32, r64;
 };
 
-template <typename T>
-__device__ __forceinline__ NbrList<T> load_nbrs(const Dev<T>& C, int i, int lane) {
-  NbrList<T> L;
+template <typename T, bool EXT = false>
+__device__ __forceinline__ NbrList<T, EXT> load_nbrs(const Dev<T>& C, int i, int lane) {
+  NbrList<T, EXT> L;
   L.id = -1; L.x = L.y = L.z = T(0); L.cand = false; L.r32 = 0.f; L.r64 = 0.f;
   if (C.knn) {
     L.id = C.knn[(long long)i * 32 + lane];
     float d32 = C.knn_d2[(long long)i * 32 + 31];
     int k32 = C.knn[(long long)i * 32 + 31];
     L.r32 = (d32 > 0.f && k32 >= 0) ? sqrtf(d32 * (1.f - 1e-6f)) : 0.f;
-    if (C.knn2 && L.r32 > 0.f) L.r64 = C.knn_r64[i];
+    if (EXT && C.knn2 && L.r32 > 0.f) L.r64 = C.knn_r64[i];
     L.cand = L.id >= 0 && ((C.cmask[i] >> lane) & 1u);
   } else if (C.ncand > 0) {
     L.id = lane < C.ncand ? C.cand[(long long)i * C.ncand + lane] : -1;
@@ -203,9 +206,9 @@ struct CornerScratch {
   int pad;
 };
 
-template <typename T, typename Exact>
+template <typename T, typename NL, typename Exact>
 __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx, T qy, T qz, T e,
-                              const int* excl, int lane, ScanScratch& S, const NbrList<T>& L, Exact& exact,
+                              const int* excl, int lane, ScanScratch& S, const NL& L, Exact& exact,
                               int* wit, int* scanned, int* listed) {
   const T U = Prec<T>::U;
   T gx = vix + qx, gy = viy + qy, gz = viz + qz;
@@ -268,7 +271,7 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
   }
   // the same with the 64 nearest, when their radius covers the ball: each lane
   // also tests its entry among the 33rd..64th (loaded here, rarely needed)
-  if (L.r64 > 0.f && L.r64 >= 2.f * (float)(di + delta) * (1.f + 2e-5f)) {
+  if (NL::ext && L.r64 > 0.f && L.r64 >= 2.f * (float)(di + delta) * (1.f + 2e-5f)) {
     *listed += 1;
     T ld = T(1e30), lo = T(1e30);
     int lk = 0x7fffffff, lok = 0x7fffffff;

@@ -272,7 +272,9 @@ constexpr int FLOOD_WARPS = 4;
 #endif
 
 // Warp per pair: each warp claims `chunk` consecutive queue slots at a time.
-template <typename T, int MODE>
+// EXT: point-in-cell tests and searches may use the 33rd..64th nearest (learned
+// form with the extended list).
+template <typename T, int MODE, bool EXT = false>
 __global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(const __grid_constant__ Dev<T> C, int chunk) {
   using W = typename WarpOf<T, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -294,8 +296,8 @@ __global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(co
 #endif
       if (key == EMPTY_KEY) { stop = true; break; }
       int a = (int)(key >> 32), i = (int)(key & 0xffffffffull);
-      if constexpr (MODE == VD_MODE_3D) c3::process_pair(C, w, a, i, (long long)h, lane);
-      else cp::process_pair<T>(C, w, a, i, (long long)h, lane);
+      if constexpr (MODE == VD_MODE_3D) c3::process_pair<EXT>(C, w, a, i, (long long)h, lane);
+      else cp::process_pair<T, EXT>(C, w, a, i, (long long)h, lane);
       __syncwarp();
       if (lane == 0) {
         __threadfence();

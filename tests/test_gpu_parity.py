@@ -154,11 +154,12 @@ def test_learned_form_equals_plain_bitwise(gpu, name, n):
     d = B.diagram_from_workload(w)
     plain = d.compute()
     for k in (8, 16, 32):
-        d.set_options(learned=1, topk=k, stats=1)
-        lr = d.compute()
-        assert lr["stats"]["learned_hits"] > 0
-        for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
-            assert torch.equal(plain[key], lr[key]), (k, key)
+        for nearest in (32, 64):  # lists of the 32 nearest, or extended to the 64 nearest
+            d.set_options(learned=1, topk=k, stats=1, mapping=1, nearest=nearest)
+            lr = d.compute()
+            assert lr["stats"]["learned_hits"] > 0 and lr["stats"]["nearest"] == nearest
+            for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+                assert torch.equal(plain[key], lr[key]), (k, nearest, key)
     d.close()
 
 
