@@ -53,8 +53,8 @@ DESC = {
 # clip kernel, from a single-pass ncu capture of the learned form (top 24, split) on
 # the full workload,
 # valid only for the kernel sources it was taken on (their hash)
-FLOOD_TRAFFIC = {"source_hash": "fb696da846c72a06",
-                 "bytes": {"shell": 1.42e9 + 0.696e9}}
+FLOOD_TRAFFIC = {"source_hash": "06f4396d637fe777",
+                 "bytes": {"shell": 1.28e9 + 0.608e9}}
 
 
 def _source_hash():
