@@ -455,8 +455,9 @@ __device__ __noinline__ void knn_scan_shell(const GridView<T>& G, int lev, int c
 
 // Warp per site: collect the sites of growing rings around v_i (each lane keeps
 // the sites it meets in its own column of shared memory), then merge the lanes'
-// sorted columns into the 32 nearest (ties: smaller index).  Once 32 collected
-// sites lie within some radius, that radius bounds the rest of the scan.
+// sorted columns into the 32 (or 64) nearest (ties: smaller index).  Once that
+// many collected sites lie within some radius, the radius bounds the rest of the
+// scan.
 // delta (optional): also writes delta_i (Sec. 5.1) from the list's first entry when
 // the scan certifies it as the nearest site, with the checks of k_delta; a site whose
 // nearest is not certified by the scan gets its own nearest-site query.
@@ -479,13 +480,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     T qx = s4.x, qy = s4.y, qz = s4.z;
     int cnt = 0;
     bool over = false;
-    T bound2 = T(1e36);  // squared radius already holding 32 collected sites
+    T bound2 = T(1e36);  // squared radius already holding `want` collected sites
     auto visit = [&](const typename Prec<T>::V4& s) {
       int k = site_id(s);
       if (k == i) return;
       T dx = s.x - qx, dy = s.y - qy, dz = s.z - qz;
       T d = dx * dx + dy * dy + dz * dz;
-      if (d > bound2) return;  // cannot be one of the 32 nearest
+      if (d > bound2) return;  // cannot be one of the `want` nearest
       if (cnt < KNN_SLOTS) {
         S.d2[cnt][lane] = (float)d;
         S.id[cnt][lane] = k;
@@ -503,7 +504,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
     C.G.cell_at(lev, qx, qy, qz, cx, cy, cz);
     // certified: every site within `cover` of v_i was stored and at least 32 of
     // the stored distances are below cover^2 (so no unseen site can be nearer
-    // than the 32nd); otherwise the list is kept for the features but flagged
+    // than the 32nd); otherwise the list is kept for the features but flagged.
+    // certified2: the same for the 64 nearest.
     bool certified = false, certified2 = false;
     T covered = T(0);    // every site within this distance of v_i has been collected
     for (int r = 1;; ++r) {
