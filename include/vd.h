@@ -48,8 +48,10 @@ enum {
   VD_ERR_UNCERTAIN = -7,  /* reserved: a sign could not be certified even in FP64
                              (reported through the stats, results still written) */
   VD_ERR_STATE = -8,      /* call out of order (e.g. vd_compute before vd_set_domain) */
-  VD_ERR_DUPLICATE = -9   /* two sites coincide: their bisector is undefined and Eq. 1 would
+  VD_ERR_DUPLICATE = -9,  /* two sites coincide: their bisector is undefined and Eq. 1 would
                              give both the same cell (found by vd_compute's nearest-site pass) */
+  VD_ERR_IO = -10         /* a model file could not be opened, read or written, or is not a
+                             model file of this library (wrong magic, size or checksum) */
 };
 
 enum { VD_F32 = 0, VD_F64 = 1 };
@@ -81,6 +83,17 @@ enum {
                                  exact tie: simplex, site, the 4 plane sources, tie flag, kind */
   VD_STAT_WHOLE_CELLS = 24,   /* split = 1: sites whose cell was computed whole (always) */
   VD_STAT_BOUNDARY_SITES = 25,/* split = 1: sites whose cell meets the boundary surface (always) */
+  VD_STAT_BISECTOR_FACES = 26,/* bisector faces (edges in 2D / on surfaces) of positive measure in
+                                 the final pieces.  Sec. 3.3: every clip of Alg. 1
+                                 contributes a face, so there it equals VD_STAT_CLIPS */
+  VD_STAT_EXCESS_CLIPS = 27,  /* clips whose bisector is not a face of positive measure of the
+                                 final piece, summed over the pieces.  Alg. 3 searches on
+                                 the virtual edge v_i -> p; when v_i lies outside the simplex the
+                                 exit point of Omega_i on it may lie outside the simplex too, so
+                                 a clip need not contribute (Sec. 4.1); with v_i inside the
+                                 simplex (or the box) every clip does, except a clip by a
+                                 certified witness after an FP32 search failed
+                                 (VD_STAT_FALLBACK) */
   VD_STAT_LIST_TESTS = 30,    /* point-in-cell tests and queries settled from the 32 nearest
                                  sites of the cell's site, with no grid scan (learned form) */
   VD_STAT_MAPPING = 31,       /* clip-kernel mapping used: mapping | chunk << 8 | list << 16
@@ -195,24 +208,57 @@ int vd_set_domain(vd_ctx* ctx, const void* verts, int64_t nv, const int32_t* sim
  * Synchronises the context stream. */
 int vd_set_box(vd_ctx* ctx, const double* lo, const double* hi);
 
-/* Replace the options (NULL restores the defaults). */
+/* Replace the options (NULL restores the defaults).  Service call: the paper
+ * fixes none of these knobs (capacities, limits and the batching / learned
+ * choices are this library's).  Drops the autotuned choice and any captured
+ * Lloyd graph. */
 int vd_set_options(vd_ctx* ctx, const vd_options* opt);
 
-/* Enqueue all later work on this cudaStream_t (NULL: legacy default stream). */
+/* Enqueue all later work on this cudaStream_t (NULL: legacy default stream).
+ * Service call (the paper has no counterpart). */
 int vd_set_stream(vd_ctx* ctx, void* cuda_stream);
 
-/* Replace the site coordinates (same n and dim; device pointer, copied). */
+/* Replace the site coordinates V (Sec. 2.1; same n and dim; device pointer,
+ * n*dim elements of the context dtype, row-major, copied on the context
+ * stream).  Also the site update of one Lloyd step (Sec. 6.4). */
 int vd_update_sites(vd_ctx* ctx, const void* sites);
 
-/* Host-pointer variant of vd_update_sites (pinned or pageable host memory). */
+/* Host-pointer variant of vd_update_sites (pinned or pageable host memory,
+ * n*dim elements; copied on the context stream through a staging buffer
+ * owned by the context). */
 int vd_update_sites_host(vd_ctx* ctx, const void* sites_host);
 
 /* Compute the clipped / restricted diagram of the current sites (Alg. 3 for
  * every (simplex, site) pair, pairs discovered by the flag propagation of
  * Alg. 4 / Alg. 5, improved search of Sec. 5.1, grid search of Sec. 5.2).
  * Synchronises the stream once at the end to read the status and counts.
- * out may be NULL.  Returns the first device-side error, if any. */
+ * out may be NULL.  Returns the first device-side error, if any.  Equivalent
+ * to vd_compute_async followed by vd_get_status and vd_get_result. */
 int vd_compute(vd_ctx* ctx, vd_result* out);
+
+/* Enqueue the work of vd_compute on the context stream and return without
+ * waiting for it or reading anything back: no host synchronisation, no
+ * allocation, no event record, so the call can be captured into a caller's
+ * CUDA graph (stream capture on the context stream) and replayed.  Results
+ * land in the context's buffers when the stream reaches the end of the work;
+ * vd_get_status then reads the device status word and the counts.  Returns
+ * VD_ERR_STATE before vd_set_domain, when the learned form wants a network
+ * that is not set, or when mapping = 0 (autotuned) has no cached choice yet:
+ * run vd_autotune (or one vd_compute) first, outside any capture. */
+int vd_compute_async(vd_ctx* ctx);
+
+/* Wait for the context stream and read back the device status word of the
+ * last vd_compute_async (or vd_compute / vd_lloyd) with its counts: *status
+ * (host int) receives VD_OK or the first device-side error code.  The call
+ * itself returns VD_OK, VD_ERR_STATE when nothing was enqueued, or
+ * VD_ERR_CUDA.  After it, vd_get_result, vd_get_pieces and
+ * vd_copy_result_host see that computation. */
+int vd_get_status(vd_ctx* ctx, int* status);
+
+/* Fill out (as vd_compute does) from the computation that vd_get_status last
+ * read back: device pointers owned by the context, counts, stats, status.
+ * No synchronisation.  VD_ERR_STATE before any status was read. */
+int vd_get_result(vd_ctx* ctx, vd_result* out);
 
 /* Autotune the clip kernel now on the current sites (batching, Sec. 4.3: one
  * persistent launch drains the pair queue): runs vd_compute's work once per
@@ -232,7 +278,10 @@ int vd_autotune(vd_ctx* ctx, int* mapping, int* chunk, float* times_ms);
 
 /* Copy the per-site measure [n], centroid [n*3] (context dtype) and, when
  * nbr_off is not NULL, the CSR (nbr_off [n+1] int64, nbr_idx [nnz] int32) of the
- * last vd_compute to host memory.  nbr_idx must hold the nnz of that result. */
+ * last vd_compute to host memory.  nbr_idx must hold the nnz of that result.
+ * The output of Sec. 2.1 (measure and centroid of Omega_i within M) and the
+ * neighbours given by the positive flags of Sec. 2.2.  Synchronises the
+ * context stream; VD_ERR_STATE before the first computation. */
 int vd_copy_result_host(vd_ctx* ctx, void* measure, void* centroid, int64_t* nbr_off, int32_t* nbr_idx);
 
 /* Lloyd's method (Sec. 6.4, density 1): iters times { compute the diagram;
@@ -241,16 +290,25 @@ int vd_copy_result_host(vd_ctx* ctx, void* measure, void* centroid, int64_t* nbr
  * the end.  The last iteration's diagram is not recomputed for the final sites. */
 int vd_lloyd(vd_ctx* ctx, int iters, int use_graph);
 
-/* Copy the current site coordinates (n*3, context dtype) to a device buffer. */
+/* Copy the current site coordinates V (Sec. 2.1; after vd_lloyd, the relaxed
+ * sites of Sec. 6.4) to a device buffer: n*3 elements of the context dtype
+ * (z = 0 in 2D), enqueued on the context stream. */
 int vd_get_sites(vd_ctx* ctx, void* sites_out);
 
-/* Per-piece output of the last vd_compute (the clip topology). */
+/* Per-piece output of the last vd_compute: every processed pair (T_a, v_i)
+ * with its piece P_{a,i} = T_a intersected with Omega_i (Sec. 2.1) and the face
+ * flags of the piece (Sec. 2.2: j >= 0 for the face on bisector B_ij, -(b+1) for
+ * the face shared with simplex b, INT32_MIN for the mesh boundary), as device
+ * arrays owned by the context (allocated on first use, valid until the next
+ * compute).  Synchronises the context stream; VD_ERR_STATE before the first
+ * computation. */
 int vd_get_pieces(vd_ctx* ctx, vd_pieces* out);
 
-/* Learned proposal (ranking of likely bisector neighbours): candidate site
- * indices per site, device int32 [n*k], -1 = unused slot; copied.  They only
- * order the search; every clip is still decided by the exact test, so the
- * output does not change.  k = 0 clears them. */
+/* Learned proposal (ranking of likely bisector neighbours; the paper has no
+ * counterpart): candidate site indices per site, device int32 [n*k], -1 =
+ * unused slot, k <= 32; copied.  They only order the bisector search of
+ * Sec. 3.2; every clip is still decided by the exact test, so the output does
+ * not change.  k = 0 clears them. */
 int vd_set_candidates(vd_ctx* ctx, const int32_t* cand, int k);
 
 /* Piece export into caller-owned device buffers, with no device allocation.
@@ -316,6 +374,21 @@ int vd_mlp_set_state(vd_ctx* ctx, const float* params, const float* adam_m, cons
  * Synchronises the context stream. */
 int vd_mlp_get_state(vd_ctx* ctx, float* params, float* adam_m, float* adam_v, int64_t* step);
 
+/* Save the network state (parameters, Adam moments and step: everything a
+ * resumed training needs) to a file: the 8 bytes "VDMLP01\0", int64
+ * VD_MLP_NPARAM, int64 step, then params, adam_m, adam_v as little-endian
+ * FP32 [VD_MLP_NPARAM] each, then the 64-bit FNV-1a hash of the preceding
+ * bytes.  VD_ERR_STATE without a network, VD_ERR_IO when the file cannot be
+ * written.  Synchronises the context stream. */
+int vd_model_save(vd_ctx* ctx, const char* path);
+
+/* Load a file written by vd_model_save into the context's network (as
+ * vd_mlp_set_state with all three arrays and the step); the learned form with
+ * proposal = VD_PROPOSAL_MLP then ranks with it.  VD_ERR_IO when the file is
+ * missing, short, not of this format or fails its hash (the state is then
+ * left unchanged).  Synchronises the context stream. */
+int vd_model_load(vd_ctx* ctx, const char* path);
+
 /* Training data from the last vd_compute (the sites must not have changed
  * since): x = the network input of every site (bf16 [n*96], may be NULL) and
  * labels = bit s set when slot s of the site's 32-NN list is in its neighbour
@@ -348,10 +421,11 @@ int vd_get_candidate_masks(vd_ctx* ctx, uint32_t* masks);
 int vd_mlp_train(vd_ctx* ctx, const void* x, const uint32_t* labels, int64_t rows, int batch, int epochs, float lr,
                  uint64_t seed, float* epoch_loss);
 
-/* Release everything owned by the context (NULL is allowed). */
+/* Release everything owned by the context (NULL is allowed).  Synchronises
+ * the context stream first.  Service call (the paper has no counterpart). */
 void vd_destroy(vd_ctx* ctx);
 
-/* Static string naming an error code. */
+/* Static string naming an error code (service call). */
 const char* vd_strerror(int code);
 
 #ifdef __cplusplus

@@ -25,7 +25,7 @@ PHASE_NAMES = ("grid", "delta", "seed", "clip", "reduce")
 
 ERRORS = {0: "ok", -1: "VD_ERR_ARG", -2: "VD_ERR_CUDA", -3: "VD_ERR_OOM", -4: "VD_ERR_CAPACITY",
           -5: "VD_ERR_LIMIT", -6: "VD_ERR_DOMAIN", -7: "VD_ERR_UNCERTAIN", -8: "VD_ERR_STATE",
-          -9: "VD_ERR_DUPLICATE"}
+          -9: "VD_ERR_DUPLICATE", -10: "VD_ERR_IO"}
 
 
 class VDError(RuntimeError):
@@ -76,6 +76,11 @@ def load(path: str = LIB_PATH):
         "vd_update_sites": ([P, P], I),
         "vd_update_sites_host": ([P, P], I),
         "vd_compute": ([P, ctypes.POINTER(Result)], I),
+        "vd_compute_async": ([P], I),
+        "vd_get_status": ([P, ctypes.POINTER(I)], I),
+        "vd_get_result": ([P, ctypes.POINTER(Result)], I),
+        "vd_model_save": ([P, ctypes.c_char_p], I),
+        "vd_model_load": ([P, ctypes.c_char_p], I),
         "vd_copy_result_host": ([P, P, P, P, P], I),
         "vd_lloyd": ([P, I, I], I),
         "vd_get_sites": ([P, P], I),
@@ -110,7 +115,8 @@ def exported_symbols():
             "vd_get_pieces", "vd_set_candidates", "vd_destroy", "vd_strerror", "vd_get_pieces_noalloc",
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
             "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box",
-            "vd_create_power2d"]
+            "vd_create_power2d", "vd_compute_async", "vd_get_status", "vd_get_result", "vd_model_save",
+            "vd_model_load"]
 
 
 class _DevArray:
@@ -175,16 +181,28 @@ class Diagram:
         if options:
             self.set_options(**options)
         if box is not None:
-            lo = (ctypes.c_double * 3)(*[float(x) for x in box[0]])
-            hi = (ctypes.c_double * 3)(*[float(x) for x in box[1]])
-            self.m, self.k = 1, 0
-            _check(lib.vd_set_box(h, lo, hi), "vd_set_box")
+            self.set_box(*box)
         else:
-            v = verts.to(self.dtype).contiguous()
-            t = simplices.to(torch.int32).contiguous()
-            self.m, self.k = t.shape
-            _check(lib.vd_set_domain(h, v.data_ptr(), v.shape[0], t.data_ptr(), self.m, self.k), "vd_set_domain")
+            self.set_domain(verts, simplices)
         self.result = None
+
+    def set_box(self, lo, hi):
+        """vd_set_box: the axis-aligned box [lo, hi] as a convex domain."""
+        lo = (ctypes.c_double * 3)(*[float(x) for x in lo])
+        hi = (ctypes.c_double * 3)(*[float(x) for x in hi])
+        _check(load().vd_set_box(self._h, lo, hi), "vd_set_box")
+        self.m, self.k = 1, 0
+
+    def set_domain(self, verts, simplices, check=True):
+        """vd_set_domain with a new mesh; returns the code when check is False."""
+        v = verts.to(self.dtype).contiguous()
+        t = simplices.to(torch.int32).contiguous()
+        code = load().vd_set_domain(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], t.shape[1])
+        if check:
+            _check(code, "vd_set_domain")
+        if code == 0:
+            self.m, self.k = t.shape
+        return code
 
     def set_options(self, **kw):
         o = Options()
@@ -213,6 +231,31 @@ class Diagram:
         r = Result()
         return load().vd_compute(self._h, ctypes.byref(r)), r
 
+    def compute_async(self):
+        """Enqueue a compute on the diagram's stream (no host synchronisation)."""
+        _check(load().vd_compute_async(self._h), "vd_compute_async")
+
+    def status(self):
+        """Wait for the stream and read the device status of the last enqueued compute."""
+        st = ctypes.c_int()
+        _check(load().vd_get_status(self._h, ctypes.byref(st)), "vd_get_status")
+        return st.value
+
+    def get_result(self, check=True):
+        """The result (copies) of the computation whose status was read last."""
+        r = Result()
+        _check(load().vd_get_result(self._h, ctypes.byref(r)), "vd_get_result")
+        if check:
+            _check(int(r.status), "device status")
+        self.result = r
+        return self._pack(r, int(r.status))
+
+    def model_save(self, path):
+        _check(load().vd_model_save(self._h, os.fsencode(path)), "vd_model_save")
+
+    def model_load(self, path):
+        _check(load().vd_model_load(self._h, os.fsencode(path)), "vd_model_load")
+
     def _pack(self, r, code):
         n = int(r.n)
         out = {
@@ -225,7 +268,8 @@ class Diagram:
             "stats": dict(zip(STAT_NAMES, [int(x) for x in r.stats][:len(STAT_NAMES)]),
                           error_line=int(r.stats[15]), diag=[int(x) for x in r.stats[16:24]],
                           list_tests=int(r.stats[30]), whole_cells=int(r.stats[24]),
-                          boundary_sites=int(r.stats[25]), mapping=int(r.stats[31]) & 255,
+                          boundary_sites=int(r.stats[25]), bisector_faces=int(r.stats[26]),
+                          excess_clips=int(r.stats[27]), mapping=int(r.stats[31]) & 255,
                           chunk=(int(r.stats[31]) >> 8) & 255, nearest=int(r.stats[31]) >> 16),
             "phase_ms": dict(zip(PHASE_NAMES, [float(x) for x in r.phase_ms][:len(PHASE_NAMES)])),
         }

@@ -125,6 +125,7 @@ struct vd_ctx {
   int last_where = 0;          // source line of the first device-side error
   unsigned long long last_stats[VD_STAT_N] = {0};
   bool computed = false;
+  bool pending = false;        // vd_compute_async enqueued work whose status is not read yet
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   cudaEvent_t ev[VD_PHASE_N + 1] = {};
@@ -381,7 +382,7 @@ static void enqueue_compute(vd_ctx* c) {
   scan_excl<int, int>(s, c->fc, c->foff, c->n + 1, (int*)c->scan_tmp);
   k_site_nbr<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, c->foff, c->tmp, c->ucnt);
   scan_excl<int, long long>(s, c->ucnt, c->noff, c->n + 1, (long long*)c->scan_tmp);
-  k_site_nbr_copy<<<bs, 128, 0, s>>>((int)c->n, c->foff, c->tmp, c->noff, c->nidx);
+  k_site_nbr_copy<<<bs, 128, 0, s>>>((int)c->n, c->foff, c->tmp, c->noff, c->nidx, c->status);
   c->launches += 5 + 3 * scan_launches(c->n + 1);
   mark(c, 5);
 }
@@ -402,10 +403,10 @@ static void enqueue_lloyd(vd_ctx* c) {
   unsigned bn = nblk(c->n, 256);
   if (c->dtype == VD_F64)
     k_lloyd<double><<<bn, 256, 0, c->stream>>>((int)c->n, (double*)c->sites, (const double*)c->measure,
-                                              (const double*)c->centroid);
+                                              (const double*)c->centroid, c->status);
   else
     k_lloyd<float><<<bn, 256, 0, c->stream>>>((int)c->n, (float*)c->sites, (const float*)c->measure,
-                                             (const float*)c->centroid);
+                                             (const float*)c->centroid, c->status);
 }
 
 template <typename T, int MODE>
@@ -580,6 +581,7 @@ const char* vd_strerror(int code) {
     case VD_ERR_UNCERTAIN: return "sign not certified in FP64";
     case VD_ERR_STATE: return "call out of order";
     case VD_ERR_DUPLICATE: return "two sites coincide";
+    case VD_ERR_IO: return "model file could not be read or written, or is not a model file";
     default: return "unknown error";
   }
 }
@@ -1078,10 +1080,44 @@ int vd_compute(vd_ctx* c, vd_result* out) {
   CK(cudaGetLastError());
   int st = read_status(c);
   c->timing_now = false;
+  c->pending = false;
   c->sites_fresh = true;
   c->knn_fresh = c->opt.learned && !c->cand;
   fill_result(c, out);
   return st;
+}
+
+int vd_compute_async(vd_ctx* c) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->have_domain) return VD_ERR_STATE;
+  if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
+  if (c->opt.mapping == 0 && !c->tuned) return VD_ERR_STATE;  // tuning synchronises: not here
+  resolve_mapping(c);
+  CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
+  c->timing_now = false;  // no event records: the work stays capturable as it is
+  enqueue_any(c);
+  CK(cudaGetLastError());
+  c->pending = true;
+  c->sites_fresh = true;
+  c->knn_fresh = c->opt.learned && !c->cand;
+  return VD_OK;
+}
+
+int vd_get_status(vd_ctx* c, int* status) {
+  if (!c || !status) return VD_ERR_ARG;
+  if (!c->pending && !c->computed) return VD_ERR_STATE;
+  int st = read_status(c);
+  if (st == VD_ERR_CUDA || st == VD_ERR_OOM) return st;  // the read itself failed
+  c->pending = false;
+  *status = st;
+  return VD_OK;
+}
+
+int vd_get_result(vd_ctx* c, vd_result* out) {
+  if (!c || !out) return VD_ERR_ARG;
+  if (!c->computed) return VD_ERR_STATE;
+  fill_result(c, out);
+  return VD_OK;
 }
 
 int vd_autotune(vd_ctx* c, int* mapping, int* chunk, float* times_ms) {
@@ -1158,7 +1194,7 @@ int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
 
 int vd_get_pieces(vd_ctx* c, vd_pieces* out) {
   if (!c || !out) return VD_ERR_ARG;
-  if (!c->computed) return VD_ERR_STATE;
+  if (!c->computed || c->last_status != VD_OK) return VD_ERR_STATE;  // failed: per-slot outputs incomplete
   long long np = c->last_pairs;
   if (!c->xs) {
     DALLOC(c->xs, int, c->qcap, true);
@@ -1170,14 +1206,14 @@ int vd_get_pieces(vd_ctx* c, vd_pieces* out) {
   CK(cudaMemsetAsync(c->pfcnt + np, 0, sizeof(int), s));
   if (c->dtype == VD_F64) {
     Dev<double> D = make_dev<double>(c);
-    k_export_ids<double><<<c->nsm * 8, 256, 0, s>>>(D, c->xs, c->xi);
+    k_export_ids<double><<<c->nsm * 8, 256, 0, s>>>(D, c->xs, c->xi, np);
     scan_excl<int, long long>(s, c->pfcnt, c->xoff, np + 1, (long long*)c->scan_tmp);
-    k_export_flags<double><<<c->nsm * 8, 256, 0, s>>>(D, c->xoff, c->xflags);
+    k_export_flags<double><<<c->nsm * 8, 256, 0, s>>>(D, c->xoff, c->xflags, np);
   } else {
     Dev<float> D = make_dev<float>(c);
-    k_export_ids<float><<<c->nsm * 8, 256, 0, s>>>(D, c->xs, c->xi);
+    k_export_ids<float><<<c->nsm * 8, 256, 0, s>>>(D, c->xs, c->xi, np);
     scan_excl<int, long long>(s, c->pfcnt, c->xoff, np + 1, (long long*)c->scan_tmp);
-    k_export_flags<float><<<c->nsm * 8, 256, 0, s>>>(D, c->xoff, c->xflags);
+    k_export_flags<float><<<c->nsm * 8, 256, 0, s>>>(D, c->xoff, c->xflags, np);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
@@ -1254,26 +1290,31 @@ int vd_get_pieces_noalloc(vd_ctx* c, int32_t* simplex, int32_t* site, int64_t* f
                           int64_t* n_pieces, int64_t* n_flags) {
   if (!c || !simplex || !site || !flag_off || !n_pieces || !n_flags || pieces_capacity < 0 || flags_capacity < 0)
     return VD_ERR_ARG;
-  if (!c->computed) return VD_ERR_STATE;
+  if (!c->computed || c->last_status != VD_OK) return VD_ERR_STATE;
   static_assert(NOALLOC_MAX_PIECES + 1 <= (1ll << 26), "scan size");
   if (scan_tmp_elems(NOALLOC_MAX_PIECES + 1) > NOALLOC_SCRATCH) return VD_ERR_CAPACITY;
   long long np = c->last_pairs;
   if (np > NOALLOC_MAX_PIECES || np > pieces_capacity) return VD_ERR_CAPACITY;
+  // the scratch address below is the one of the context's device: kernels launched
+  // with another device current would be handed a foreign address
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != c->device) return VD_ERR_ARG;
   long long* scratch = nullptr;
   int rc = noalloc_scratch(c->device, &scratch);
   if (rc) return rc;
   cudaStream_t s = c->stream;
   long long* off = reinterpret_cast<long long*>(flag_off);
   CK(cudaMemsetAsync(c->pfcnt + np, 0, sizeof(int), s));
-  if (c->dtype == VD_F64) k_export_ids<double><<<c->nsm * 8, 256, 0, s>>>(make_dev<double>(c), simplex, site);
-  else k_export_ids<float><<<c->nsm * 8, 256, 0, s>>>(make_dev<float>(c), simplex, site);
+  if (c->dtype == VD_F64) k_export_ids<double><<<c->nsm * 8, 256, 0, s>>>(make_dev<double>(c), simplex, site, np);
+  else k_export_ids<float><<<c->nsm * 8, 256, 0, s>>>(make_dev<float>(c), simplex, site, np);
   scan_excl<int, long long>(s, c->pfcnt, off, np + 1, scratch);
   long long total = 0;
   CK(cudaMemcpyAsync(&total, off + np, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (total > flags_capacity || (total > 0 && !flags)) return VD_ERR_CAPACITY;
-  if (c->dtype == VD_F64) k_export_flags<double><<<c->nsm * 8, 256, 0, s>>>(make_dev<double>(c), off, flags);
-  else k_export_flags<float><<<c->nsm * 8, 256, 0, s>>>(make_dev<float>(c), off, flags);
+  if (c->dtype == VD_F64) k_export_flags<double><<<c->nsm * 8, 256, 0, s>>>(make_dev<double>(c), off, flags, np);
+  else k_export_flags<float><<<c->nsm * 8, 256, 0, s>>>(make_dev<float>(c), off, flags, np);
   size_t ts = tsize(c->dtype);
   if (measure && np) CK(cudaMemcpyAsync(measure, c->pmeas, (size_t)np * ts, cudaMemcpyDeviceToDevice, s));
   if (moment && np) CK(cudaMemcpyAsync(moment, c->pm1, (size_t)np * 3 * ts, cudaMemcpyDeviceToDevice, s));
@@ -1396,6 +1437,69 @@ int vd_mlp_get_state(vd_ctx* c, float* params, float* adam_m, float* adam_v, int
   if (adam_v) CK(cudaMemcpyAsync(adam_v, c->mlp_v, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   if (step) *step = c->mlp_step;
+  return VD_OK;
+}
+
+// ---- model file: magic, nparam, step, params, adam_m, adam_v, FNV-1a of all that ----
+namespace {
+const char kModelMagic[8] = {'V', 'D', 'M', 'L', 'P', '0', '1', '\0'};
+
+unsigned long long fnv1a(const unsigned char* p, size_t n, unsigned long long h) {
+  for (size_t k = 0; k < n; ++k) { h ^= p[k]; h *= 0x100000001b3ull; }
+  return h;
+}
+}  // namespace
+
+int vd_model_save(vd_ctx* c, const char* path) {
+  if (!c || !path) return VD_ERR_ARG;
+  if (!c->mlp_ready) return VD_ERR_STATE;
+  const size_t np = mlp::NPARAM;
+  std::vector<unsigned char> buf(8 + 16 + 3 * np * sizeof(float));
+  std::memcpy(buf.data(), kModelMagic, 8);
+  long long hdr[2] = {(long long)np, c->mlp_step};
+  std::memcpy(buf.data() + 8, hdr, 16);
+  float* body = reinterpret_cast<float*>(buf.data() + 24);
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(body, c->mlp_p, np * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(body + np, c->mlp_m, np * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(body + 2 * np, c->mlp_v, np * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  unsigned long long h = fnv1a(buf.data(), buf.size(), 0xcbf29ce484222325ull);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return VD_ERR_IO;
+  bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() && std::fwrite(&h, 8, 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? VD_OK : VD_ERR_IO;
+}
+
+int vd_model_load(vd_ctx* c, const char* path) {
+  if (!c || !path) return VD_ERR_ARG;
+  const size_t np = mlp::NPARAM;
+  std::vector<unsigned char> buf(8 + 16 + 3 * np * sizeof(float));
+  unsigned long long h = 0;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return VD_ERR_IO;
+  bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size() && std::fread(&h, 8, 1, f) == 1;
+  unsigned char extra;
+  ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing after the hash
+  std::fclose(f);
+  if (!ok || std::memcmp(buf.data(), kModelMagic, 8) != 0) return VD_ERR_IO;
+  long long hdr[2];
+  std::memcpy(hdr, buf.data() + 8, 16);
+  if (hdr[0] != (long long)np || hdr[1] < 0) return VD_ERR_IO;
+  if (fnv1a(buf.data(), buf.size(), 0xcbf29ce484222325ull) != h) return VD_ERR_IO;
+  int rc = mlp_alloc(c);
+  if (rc) return rc;
+  const float* body = reinterpret_cast<const float*>(buf.data() + 24);
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->mlp_p, body, np * sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->mlp_m, body + np, np * sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->mlp_v, body + 2 * np, np * sizeof(float), cudaMemcpyHostToDevice, s));
+  mlp::k_to_bf16<<<nblk(mlp::NPARAM, 256), 256, 0, s>>>(c->mlp_p, c->mlp_wb);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  c->mlp_step = hdr[1];
+  c->mlp_ready = true;
   return VD_OK;
 }
 

@@ -50,7 +50,12 @@ struct Masks {
   unsigned long long palive;
 };
 
-__device__ __forceinline__ bool bit(const unsigned* m, int t) { return (m[t >> 5] >> (t & 31)) & 1u; }
+// bit t of a 96-bit mask held as three words (selects, not a run-time array index,
+// so that masks in registers stay there)
+__device__ __forceinline__ bool bit(const unsigned* m, int t) {
+  unsigned w = t < 32 ? m[0] : (t < 64 ? m[1] : m[2]);
+  return (w >> (t & 31)) & 1u;
+}
 
 __device__ __forceinline__ int nth_set(unsigned m, int k) {
   int pos = 0;
@@ -106,11 +111,15 @@ __device__ void plane_face(const Dev<float>& C, int a, int f, float3 vi, float4&
   M = make_float2(mx + my + mz, mx * fabsf(ax) + my * fabsf(ay) + mz * fabsf(az));
 }
 
-__device__ __forceinline__ void plane_bis(const Dev<float>& C, int j, float3 vi, float4& P, float2& M) {
-  float wx = C.sites[3 * j] - vi.x, wy = C.sites[3 * j + 1] - vi.y, wz = C.sites[3 * j + 2] - vi.z;
+__device__ __forceinline__ void plane_bis_at(float sx, float sy, float sz, float3 vi, float4& P, float2& M) {
+  float wx = sx - vi.x, wy = sy - vi.y, wz = sz - vi.z;
   float c = 0.5f * (wx * wx + wy * wy + wz * wz);
   P = make_float4(wx, wy, wz, c);
   M = make_float2(fabsf(wx) + fabsf(wy) + fabsf(wz), c);
+}
+
+__device__ __forceinline__ void plane_bis(const Dev<float>& C, int j, float3 vi, float4& P, float2& M) {
+  plane_bis_at(C.sites[3 * j], C.sites[3 * j + 1], C.sites[3 * j + 2], vi, P, M);
 }
 
 // float64 plane from its source, with running error bounds
@@ -302,6 +311,24 @@ __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const NL
   return nn_query(C, W, px, py, pz, lane, K);
 }
 
+// Coordinates of site k (warp-uniform k >= 0): shuffled from the lane whose
+// listed site it is, else loaded (one of the 33rd..64th nearest, or unlisted).
+template <typename NL>
+__device__ __forceinline__ void listed_coords(const Dev<float>& C, const NL& L, int k, int lane, float& x, float& y,
+                                              float& z) {
+  unsigned m = __ballot_sync(FULL, L.id == k && k >= 0);
+  if (m) {
+    int src = __ffs(m) - 1;
+    x = __shfl_sync(FULL, L.x, src);
+    y = __shfl_sync(FULL, L.y, src);
+    z = __shfl_sync(FULL, L.z, src);
+  } else if (k >= 0) {
+    x = C.sites[3 * k]; y = C.sites[3 * k + 1]; z = C.sites[3 * k + 2];
+  } else {
+    x = y = z = 0.f;
+  }
+}
+
 // Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
 // Returns the bisector site j for the outside corner t.
 template <typename NL>
@@ -324,9 +351,12 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, const N
     unsigned nc = __ballot_sync(FULL, L.cand);
     int wl = nc == FULL ? -1 : __ffs(~nc) - 1;
     int k = L.cand ? L.id : (lane == wl ? wit : -1);
+    // the witness's coordinates: from the lane that lists it (a register shuffle),
+    // else from memory
+    float wx_, wy_, wz_;
+    listed_coords(C, L, wit, lane, wx_, wy_, wz_);
     if (k >= 0 && k != i) {
-      float kx = L.cand ? L.x : C.sites[3 * k], ky = L.cand ? L.y : C.sites[3 * k + 1],
-            kz = L.cand ? L.z : C.sites[3 * k + 2];
+      float kx = L.cand ? L.x : wx_, ky = L.cand ? L.y : wy_, kz = L.cand ? L.z : wz_;
       float wx = kx - vi.x, wy = ky - vi.y, wz = kz - vi.z;
       float den = wx * q.x + wy * q.y + wz * q.z;
       if (den > 0.f) {
@@ -385,38 +415,22 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
     R[r] = 0;
   }
   if (!bit(om, p)) { set_error(C.status, VD_ERR_LIMIT); return -1; }
-  R[p >> 5] = 1u << (p & 31);
-  for (int it = 0; it < MAXT; ++it) {
-    unsigned nR[3];
-    bool ch = false;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      int t = r * 32 + lane;
-      bool add = false;
-      if (bit(om, t) && !bit(R, t)) {
-        uchar4 nb = W.tn[t];
-        add = bit(R, nb.x) || bit(R, nb.y) || bit(R, nb.z);
-      }
-      nR[r] = R[r] | __ballot_sync(FULL, add);
-      ch |= nR[r] != R[r];
-    }
-    R[0] = nR[0]; R[1] = nR[1]; R[2] = nR[2];
-    if (!ch) break;
-  }
+  // The corners beyond a plane of a convex polytope are connected through its
+  // edges, and every side decision here is exact, so R_p (Sec. 5.3) is the whole
+  // outside set: no search over the dual mesh is needed.
+  R[0] = om[0]; R[1] = om[1]; R[2] = om[2];
   if (R[0] == Mk.alive[0] && R[1] == Mk.alive[1] && R[2] == Mk.alive[2]) return 1;
-  // boundary edges of R: (x -> y) of a removed corner whose neighbour u is kept.
-  // Each lane lists its edges (at most 3 corners x 3 edges), packed x | y << 8 | u << 16.
+  // boundary edges of R: (x -> y) of a removed corner whose neighbour u is kept,
+  // packed x | y << 8 | u << 16; counted first, then written straight to shared
+  // memory at the lane's offset (lane order, corner slots, edges x->y, y->z, z->x)
   int cnt = 0;
-  unsigned edge[9];
-#pragma unroll 1
+#pragma unroll
   for (int r = 0; r < 3; ++r) {
     int t = r * 32 + lane;
-    if (!bit(R, t)) continue;
-    uchar4 v = W.tv[t], nb = W.tn[t];
-    int vv[3] = {v.x, v.y, v.z}, nn[3] = {nb.x, nb.y, nb.z};
-#pragma unroll 1
-    for (int e = 0; e < 3; ++e)
-      if (!bit(R, nn[e])) edge[cnt++] = (unsigned)vv[e] | ((unsigned)vv[(e + 1) % 3] << 8) | ((unsigned)nn[e] << 16);
+    if (bit(R, t)) {
+      uchar4 nb = W.tn[t];
+      cnt += (int)!bit(R, nb.x) + (int)!bit(R, nb.y) + (int)!bit(R, nb.z);
+    }
   }
   unsigned fr[3] = {~Mk.alive[0] | R[0], ~Mk.alive[1] | R[1], ~Mk.alive[2] | R[2]};
   int nfree = __popc(fr[0]) + __popc(fr[1]) + __popc(fr[2]);
@@ -431,8 +445,19 @@ __device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a
   unsigned* ebuf = reinterpret_cast<unsigned*>(W.contrib);
   int* sbuf = reinterpret_cast<int*>(ebuf + MAXT);
   __syncwarp();
-#pragma unroll 1
-  for (int c = 0; c < cnt; ++c) ebuf[base + c] = edge[c];
+  {
+    int c = base;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      int t = r * 32 + lane;
+      if (bit(R, t)) {
+        uchar4 v = W.tv[t], nb = W.tn[t];
+        if (!bit(R, nb.x)) ebuf[c++] = (unsigned)v.x | ((unsigned)v.y << 8) | ((unsigned)nb.x << 16);
+        if (!bit(R, nb.y)) ebuf[c++] = (unsigned)v.y | ((unsigned)v.z << 8) | ((unsigned)nb.y << 16);
+        if (!bit(R, nb.z)) ebuf[c++] = (unsigned)v.z | ((unsigned)v.x << 8) | ((unsigned)nb.z << 16);
+      }
+    }
+  }
   __syncwarp();
   // reset the loop maps, then claim them
 #pragma unroll 1
@@ -850,7 +875,11 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
     int pl = __ffsll((long long)freep) - 1;
     float4 P;
     float2 M;
-    plane_bis(C, j, vi, P, M);
+    {
+      float jx, jy, jz;
+      listed_coords(C, L, j, lane, jx, jy, jz);
+      plane_bis_at(jx, jy, jz, vi, P, M);
+    }
     add_plane(W, pl, P, M, j, lane);
     if (side_of(C, W, a, i, p, pl) >= 0) {
       // FP32 search landed on a bisector that does not cut p: use the certified closer site
@@ -875,7 +904,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   // faces of positive area: output flags and propagate (Alg. 4 / Alg. 5 rules)
   int nflag = 0;
   int myflag[2];
-  bool has[2] = {false, false};
+  bool has[2] = {false, false}, bis[2] = {false, false};
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     int x = lane + 32 * h;
@@ -883,6 +912,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       float ax = W.parea[x][0], ay = W.parea[x][1], az = W.parea[x][2];
       if (ax * ax + ay * ay + az * az > 0.f) {
         int src = W.psrc[x];
+        bis[h] = src >= 0;
         if (src >= 0) {
           myflag[h] = src;
           // the box form seeds every site itself; the split propagates through
@@ -901,6 +931,8 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   }
   unsigned b0 = __ballot_sync(FULL, has[0]), b1 = __ballot_sync(FULL, has[1]);
   nflag = __popc(b0) + __popc(b1);
+  // bisector faces of the final piece: each clip that contributed left one (Sec. 3.3)
+  unsigned nbis = C.want_stats ? __popc(__ballot_sync(FULL, bis[0])) + __popc(__ballot_sync(FULL, bis[1])) : 0u;
   long long fbase = 0;
   if (lane == 0 && nflag) fbase = (long long)atomicAdd(C.ctr + CTR_FLAGS, (unsigned long long)nflag);
   fbase = __shfl_sync(FULL, fbase, 0);
@@ -926,6 +958,8 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       stat_add(C, VD_STAT_FALLBACK, K.fallback);
       stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
       stat_add(C, VD_STAT_LIST_TESTS, K.list);
+      stat_add(C, VD_STAT_BISECTOR_FACES, nbis);
+      stat_add(C, VD_STAT_EXCESS_CLIPS, K.clips > nbis ? K.clips - nbis : 0u);
     }
   }
   __syncwarp();

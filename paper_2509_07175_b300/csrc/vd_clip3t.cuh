@@ -98,6 +98,7 @@ __device__ __forceinline__ bool any_cand(const TList& L, int i) {
 struct Counters {
   unsigned nn, corner, clips, lam, search, learned, fallback, list;
   unsigned long long scanned;
+  unsigned bisf, excess;  // bisector faces of the final pieces; clips that left none
 };
 
 // ----- nearest-site queries -------------------------------------------------------
@@ -624,6 +625,7 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
   }
   bool empty = false;
   int nclip = 0;
+  unsigned pclips = 0;
   for (;;) {
     int p = -1;
     for (;;) {
@@ -659,6 +661,7 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
     }
     int rc = t_clip(C, P, Mk, a, i, pl, p);
     K.clips++;
+    ++pclips;
     if (rc < 0) return;
     if (rc == 1) { empty = true; break; }
   }
@@ -670,6 +673,7 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
   int nflag = nonempty ? __popcll(posarea) : 0;
   long long fbase = nflag ? (long long)atomicAdd(C.ctr + CTR_FLAGS, (unsigned long long)nflag) : 0;
   if (fbase + nflag > C.fcap) { set_error(C.status, VD_ERR_CAPACITY); return; }
+  unsigned nbis = 0;
   if (nflag) {
     int w = 0;
     unsigned long long m = posarea;
@@ -677,6 +681,7 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
       int x = __ffsll((long long)m) - 1;
       m &= m - 1;
       int src = P.psrc[x], flag;
+      nbis += src >= 0;
       if (src >= 0) {
         flag = src;
         push_pair(C, a, src);
@@ -694,6 +699,8 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
   C.pm1[3 * slot + 2] = nonempty ? m1.z : 0.f;
   C.pfoff[slot] = fbase;
   C.pfcnt[slot] = nflag;
+  K.bisf += nbis;
+  K.excess += pclips > nbis ? pclips - nbis : 0u;
 }
 
 }  // namespace c3t

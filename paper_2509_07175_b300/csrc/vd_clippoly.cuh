@@ -482,13 +482,14 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
     nonempty = area > T(0);
   }
   // edges of positive length: flags and propagation
-  bool has = false;
+  bool has = false, bis = false;
   int flag = 0;
   if (nonempty && lane < nv) {
     V4 A = W.vq[lane], B = W.vq[(lane + 1) % nv];
     T lx = B.x - A.x, ly = B.y - A.y, lz = B.z - A.z;
     if (lx * lx + ly * ly + lz * lz > T(0)) {
       int src = W.psrc[W.ve[lane]];
+      bis = src >= 0;
       if (src >= 0) {
         flag = src;
         push_pair(C, a, src);
@@ -503,6 +504,7 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
   }
   unsigned bm = __ballot_sync(FULL, has);
   int nflag = __popc(bm);
+  unsigned nbis = C.want_stats ? __popc(__ballot_sync(FULL, bis)) : 0u;
   long long fbase = 0;
   if (lane == 0 && nflag) fbase = (long long)atomicAdd(C.ctr + CTR_FLAGS, (unsigned long long)nflag);
   fbase = __shfl_sync(FULL, fbase, 0);
@@ -525,6 +527,8 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       stat_add(C, VD_STAT_FALLBACK, K.fallback);
       stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
       stat_add(C, VD_STAT_LIST_TESTS, K.list);
+      stat_add(C, VD_STAT_BISECTOR_FACES, nbis);
+      stat_add(C, VD_STAT_EXCESS_CLIPS, K.clips > nbis ? K.clips - nbis : 0u);
     }
   }
   __syncwarp();

@@ -189,8 +189,9 @@ __global__ void k_power_lift(const float* xy, const float* w, long long n, const
 __global__ void k_seed_box(Dev<float> C) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= C.n) return;
-  C.queue[t] = pair_key(0, site_id(C.G.L[0].gs[t]));
   if (t == 0) atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)C.n);
+  if ((long long)t >= C.qcap) { set_error(C.status, VD_ERR_CAPACITY); return; }
+  C.queue[t] = pair_key(0, site_id(C.G.L[0].gs[t]));
 }
 
 struct Locator {
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(co
 
 __global__ void __launch_bounds__(FLOOD_T_THREADS, FLOOD_T_MIN_BLOCKS) k_flood_thread(const __grid_constant__ Dev<float> C, int chunk) {
   c3t::Poly P;
-  c3t::Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  c3t::Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned m = __activemask();
@@ -351,6 +352,8 @@ __global__ void __launch_bounds__(FLOOD_T_THREADS, FLOOD_T_MIN_BLOCKS) k_flood_t
     stat_add(C, VD_STAT_FALLBACK, K.fallback);
     stat_add(C, VD_STAT_LEARNED_HITS, K.learned);
     stat_add(C, VD_STAT_LIST_TESTS, K.list);
+    stat_add(C, VD_STAT_BISECTOR_FACES, K.bisf);
+    stat_add(C, VD_STAT_EXCESS_CLIPS, K.excess);
   }
 }
 
@@ -604,6 +607,13 @@ __global__ void k_cand_by_distance(int n, int k, unsigned* cmask) {
 // per-site reduction, deterministic: the pieces of a site are summed in order
 // of their simplex index whatever order the flood produced them in
 // ---------------------------------------------------------------------------
+// The kernels that read the flood's per-slot outputs (split marks, per-site
+// reduction, export) run after it.  A device-side error leaves the outputs of
+// unfinished pairs unwritten (stale offsets and counts), so each of them
+// returns at once when the status is set.
+template <typename T>
+__device__ __forceinline__ bool failed(const Dev<T>& C) { return *(volatile const int*)C.status != 0; }
+
 template <typename T>
 __device__ __forceinline__ long long npairs(const Dev<T>& C) {
   unsigned long long t = C.ctr[CTR_TAIL];
@@ -623,6 +633,7 @@ __device__ __forceinline__ long long npairs(const Dev<T>& C) {
 // counts them.
 __global__ void k_split_mark(const __grid_constant__ Dev<float> S, const int* btet, int* bnd,
                              unsigned long long* seeds) {
+  if (failed(S)) return;
   long long np = npairs(S);
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long p0 = (long long)blockIdx.x * blockDim.x; p0 < np; p0 += stride) {
@@ -746,6 +757,7 @@ __global__ void k_split_site(const __grid_constant__ Dev<float> C, Locator L, co
 
 template <typename T>
 __global__ void k_site_count(Dev<T> C, int* scnt) {
+  if (failed(C)) return;
   long long np = npairs(C);
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
     if (C.pmeas[p] > T(0)) atomicAdd(scnt + (int)(C.queue[p] & 0xffffffffull), 1);
@@ -753,6 +765,7 @@ __global__ void k_site_count(Dev<T> C, int* scnt) {
 
 template <typename T>
 __global__ void k_site_fill(Dev<T> C, const int* soff, int* scur, int* slist) {
+  if (failed(C)) return;
   long long np = npairs(C);
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
     if (C.pmeas[p] > T(0)) {
@@ -764,7 +777,7 @@ __global__ void k_site_fill(Dev<T> C, const int* soff, int* scur, int* slist) {
 template <typename T>
 __global__ void k_site_reduce(Dev<T> C, const int* soff, int* slist, T* measure, T* centroid, int* fc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C.n) return;
+  if (i >= C.n || failed(C)) return;
   int b = soff[i], e = soff[i + 1];
   for (int u = b + 1; u < e; ++u) {  // insertion sort by simplex index
     int pu = slist[u];
@@ -795,7 +808,7 @@ __global__ void k_site_reduce(Dev<T> C, const int* soff, int* slist, T* measure,
 template <typename T>
 __global__ void k_site_nbr(Dev<T> C, const int* soff, const int* slist, const int* foff, int* tmp, int* ucnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C.n) return;
+  if (i >= C.n || failed(C)) return;
   int base = foff[i], c = 0;
   for (int u = soff[i]; u < soff[i + 1]; ++u) {
     int p = slist[u];
@@ -818,27 +831,33 @@ __global__ void k_site_nbr(Dev<T> C, const int* soff, const int* slist, const in
   ucnt[i] = c;
 }
 
-__global__ void k_site_nbr_copy(int n, const int* foff, const int* tmp, const long long* noff, int* nidx) {
+__global__ void k_site_nbr_copy(int n, const int* foff, const int* tmp, const long long* noff, int* nidx,
+                                const int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || *(volatile const int*)status != 0) return;
   long long o = noff[i];
   int c = (int)(noff[i + 1] - o);
   for (int k = 0; k < c; ++k) nidx[o + k] = tmp[foff[i] + k];
 }
 
+// v_i <- centroid_i (Sec. 6.4); after a failed compute the sites stay as they are
+// (the reduction did not run, so measure and centroid are not this iterate's)
 template <typename T>
-__global__ void k_lloyd(int n, T* sites, const T* measure, const T* centroid) {
+__global__ void k_lloyd(int n, T* sites, const T* measure, const T* centroid, const int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || !(measure[i] > T(0))) return;
+  if (i >= n || *(volatile const int*)status != 0 || !(measure[i] > T(0))) return;
   sites[3 * i] = centroid[3 * i];
   sites[3 * i + 1] = centroid[3 * i + 1];
   sites[3 * i + 2] = centroid[3 * i + 2];
 }
 
-// piece export: simplex / site of every processed pair and its flags as a CSR
+// piece export: simplex / site of every processed pair and its flags as a CSR.
+// limit: the piece count the host checked the output buffers against; the
+// kernels never write past it even if the device count were larger.
 template <typename T>
-__global__ void k_export_ids(Dev<T> C, int* ps, int* pi) {
+__global__ void k_export_ids(Dev<T> C, int* ps, int* pi, long long limit) {
   long long np = npairs(C);
+  np = np < limit ? np : limit;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
     unsigned long long key = C.queue[p];
     ps[p] = (int)(key >> 32);
@@ -847,8 +866,9 @@ __global__ void k_export_ids(Dev<T> C, int* ps, int* pi) {
 }
 
 template <typename T>
-__global__ void k_export_flags(Dev<T> C, const long long* xoff, int* xflags) {
+__global__ void k_export_flags(Dev<T> C, const long long* xoff, int* xflags, long long limit) {
   long long np = npairs(C);
+  np = np < limit ? np : limit;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x)
     for (int f = 0; f < C.pfcnt[p]; ++f) xflags[xoff[p] + f] = C.pflags[C.pfoff[p] + f];
 }

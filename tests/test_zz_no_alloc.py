@@ -78,3 +78,44 @@ def test_noalloc_export_fp64_planar(gpu):
         assert rc == 0
         _check_same(ref, got, np_, nf)
     d.close()
+
+
+def _buffers(np_cap, nf_cap, dtype):
+    return dict(simplex=torch.full((np_cap,), -7, dtype=torch.int32, device="cuda"),
+                site=torch.full((np_cap,), -7, dtype=torch.int32, device="cuda"),
+                flag_off=torch.full((np_cap + 1,), -7, dtype=torch.int64, device="cuda"),
+                flags=torch.full((max(nf_cap, 1),), -7, dtype=torch.int32, device="cuda"),
+                measure=torch.full((np_cap,), -7.0, dtype=dtype, device="cuda"),
+                moment=torch.full((np_cap, 3), -7.0, dtype=dtype, device="cuda"))
+
+
+def _call_into(d, b, np_cap, nf_cap):
+    n_p, n_f = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    rc = B.load().vd_get_pieces_noalloc(d._h, b["simplex"].data_ptr(), b["site"].data_ptr(),
+                                        b["flag_off"].data_ptr(), b["flags"].data_ptr(), b["measure"].data_ptr(),
+                                        b["moment"].data_ptr(), np_cap, nf_cap, ctypes.byref(n_p),
+                                        ctypes.byref(n_f))
+    return rc, n_p.value, n_f.value
+
+
+def test_noalloc_on_fresh_context_allocates_nothing(gpu):
+    """On a context whose pieces were never exported, two no-allocation calls in a
+    row into buffers the caller made beforehand leave the device's free memory as
+    it was, and a later vd_get_pieces gives the same pieces."""
+    w = I.workload("cube", n=8000)
+    d = B.diagram_from_workload(w)
+    r = d.compute()
+    np_ = int(r["stats"]["pairs"])
+    nf_cap = 64 * np_
+    bufs = [_buffers(np_, nf_cap, d.dtype) for _ in range(2)]
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    out = [_call_into(d, b, np_, nf_cap) for b in bufs]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    ref = d.pieces()
+    for (rc, n_p, n_f), b in zip(out, bufs):
+        assert rc == 0, B.ERRORS.get(rc, rc)
+        _check_same(ref, b, n_p, n_f)
+    d.close()
