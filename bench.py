@@ -12,7 +12,10 @@ e2e     the same metric through the public API with host buffers: pinned host
 roofline  the clip kernel (dominant), FP32-ALU bound: algorithmic FLOPs (8 per
         site-distance evaluation, counted by the library's counters) over its
         event-timed duration, against SMs x 128 lanes x 2 x max SM clock.
-cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
+cpu_baseline  the FP64 CPU oracle on the whole workload (all host threads; one
+        thread on a bounded sample), with the measured errors of the timed
+        result against it (oracle_check) and the paper's serial method on one
+        thread (serial_baseline).
 
 Multi-GPU (torchrun): independent replicas (different seeds), no data-path
 collective; value = cells of all ranks / max over ranks of the step time.
@@ -46,6 +49,10 @@ DESC = {
     "box5m": "3D clipped VD: unit cube as one convex domain (box form), 5,000,000 uniform sites (white noise), FP32",
     "grid5m": "3D clipped VD: unit cube as one convex domain (box form), 171^3 = 5,000,211 sites on a "
               "perturbed grid (+-0.1 h), FP32",
+    "blue5m": "3D clipped VD: unit cube as one convex domain (box form), 5,000,000 blue-noise sites: the "
+              "white-noise sites relaxed by 100 graph-captured Lloyd iterations of this library (timed), FP32",
+    "blue100k": "3D clipped VD: unit cube as one convex domain (box form), 100,000 Poisson-disk (blue noise) "
+                "sites, FP32",
 }
 
 
@@ -158,46 +165,165 @@ def whole_job_rate(units_per_rank: int, steps: int, world: int, max_ms: float) -
     return units_per_rank * steps * world / (max_ms / 1e3)
 
 
-def cpu_baseline(w, budget_s=15.0, seed=0):
-    """Oracle (FP64, all host threads) on a bounded sample of sites: cells/s."""
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(w, one_thread_s=8.0, seed=0):
+    """The FP64 oracle on the host cores: the whole workload on all threads (its
+    result also gives the bench line's measured errors), and a bounded sample of
+    sites on one thread.  Returns (baseline dict, oracle pieces)."""
     import numpy as np
 
     import oracle as O
 
     cores = os.cpu_count() or 1
-    o = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], nthreads=cores)
-    rng = np.random.default_rng(seed)
     n = len(w["sites"])
-    pilot = rng.choice(n, min(n, 4 * cores), replace=False)
+    o = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], nthreads=cores)
     t0 = time.perf_counter()
-    o.site_pieces(pilot)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    k = int(min(n, max(len(pilot), len(pilot) * budget_s / dt)))
-    pick = rng.choice(n, k, replace=False)
-    t0 = time.perf_counter()
-    o.site_pieces(pick)
+    op = o.all_sites()
     dt = time.perf_counter() - t0
     o.close()
-    return {"value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"all pieces of {k} random sites of the workload ({dt:.1f} s)"}
+    o1 = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], nthreads=1)
+    rng = np.random.default_rng(seed)
+    pilot = rng.choice(n, min(n, 64), replace=False)
+    t1 = time.perf_counter()
+    o1.site_pieces(pilot)
+    dp = max(time.perf_counter() - t1, 1e-6)
+    k = int(min(n, max(len(pilot), len(pilot) * one_thread_s / dp)))
+    pick = rng.choice(n, k, replace=False)
+    t1 = time.perf_counter()
+    o1.site_pieces(pick)
+    d1 = time.perf_counter() - t1
+    o1.close()
+    base = {"value": n / dt, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"whole workload: all {n} sites, every piece ({dt:.1f} s on {cores} threads)",
+            "one_thread": {"value": k / d1, "unit": UNIT, "cores": 1,
+                           "sample": f"all pieces of {k} random sites ({d1:.1f} s, 1 thread)"}}
+    return base, op
+
+
+def oracle_errors(w, res, op):
+    """Measured errors of a computed result against the oracle's whole-workload
+    pieces: per-site measure (relative), centroid (|dc| / |c| and |dc| / h_i with
+    h_i = measure^(1/d)), and whether every site's neighbour list is identical."""
+    import numpy as np
+
+    n = len(w["sites"])
+    keep = op.meas > 0
+    oi = np.asarray(op.i, dtype=np.int64)
+    om = np.zeros(n)
+    m1 = np.zeros((n, 3))
+    np.add.at(om, oi[keep], op.meas[keep])
+    np.add.at(m1, oi[keep], op.m1[keep])
+    oc = np.asarray(w["sites"], dtype=np.float64).copy()
+    ok = om > 0
+    oc[ok] += m1[ok] / om[ok, None]
+    gm = res["measure"].double().cpu().numpy()
+    gc = res["centroid"].double().cpu().numpy()
+    rel = np.abs(gm[ok] - om[ok]) / om[ok]
+    dc = np.linalg.norm(gc - oc, axis=1)
+    dim = 3 if w["mode"] == 4 else 2
+    h = om[ok] ** (1.0 / dim)
+    # neighbours: unique bisector flags of faces of positive measure, per site
+    cnt = np.diff(op.foff)
+    own = np.repeat(np.arange(len(op.meas)), cnt)
+    fl = np.asarray(op.flags, dtype=np.int64)
+    sel = keep[own] & (fl >= 0)
+    packed = np.unique((oi[own[sel]] << 32) | fl[sel])   # sorted unique (site, neighbour)
+    pairs = np.stack([packed >> 32, packed & 0xFFFFFFFF], 1) if len(packed) else np.zeros((0, 2), np.int64)
+    off = np.concatenate([[0], np.cumsum(np.bincount(pairs[:, 0], minlength=n))])
+    same_nbr = bool(np.array_equal(res["nbr_off"].cpu().numpy(), off) and
+                    np.array_equal(res["nbr_idx"].cpu().numpy().astype(np.int64), pairs[:, 1]))
+    return {"sites_checked": int(n), "max_meas_rel": float(rel.max(initial=0)),
+            "max_cent_rel": float((dc / np.maximum(np.linalg.norm(oc, axis=1), 1e-30)).max(initial=0)),
+            "max_dc_over_h": float((dc[ok] / h).max(initial=0)), "empty_cells_match": bool(((gm > 0) == ok).all()),
+            "neighbours_identical": same_nbr, "oracle_pieces": int(keep.sum()),
+            "oracle_uncertain": int(op.stats.get("uncertain", 0))}
+
+
+def serial_baseline(w, total_pieces, budget_s=8.0, seed=0):
+    """The paper's serial method (Alg. 1 + Alg. 2) on one thread over a random
+    sample of the simplices, scaled to the workload by its share of the pieces."""
+    import numpy as np
+
+    from paper_2509_07175_b300 import serial as S
+
+    m = len(w["simp"])
+    per_simplex = total_pieces / max(1, m)
+    if per_simplex * 2e-4 > budget_s:   # one simplex alone is beyond the budget (~0.2 ms per piece)
+        return {"value": None, "reason": f"{per_simplex:.0f} pieces per simplex: no bounded sample of whole simplices"}
+    t0 = time.perf_counter()
+    sv = S.Serial(w["mode"], w["sites"], w["verts"], w["simp"])
+    setup = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(m)
+    done, pieces, t_run, k = 0, 0, 0.0, 1
+    while done < m and t_run < budget_s:
+        take = order[done:done + k]
+        t1 = time.perf_counter()
+        r = sv.run_list(take)
+        t_run += time.perf_counter() - t1
+        pieces += int((r.meas > 0).sum())
+        done += len(take)
+        per = t_run / done   # seconds per simplex so far: the next batch fits the rest of the budget
+        k = int(max(1, min(2 * k, (budget_s - t_run) / max(per, 1e-9), m - done)))
+    sv.close()
+    frac = pieces / max(1, total_pieces)
+    est = setup + t_run / max(frac, 1e-12)
+    return {"value": len(w["sites"]) / est, "unit": UNIT, "cores": 1, "kind": "serial Alg. 1 + Alg. 2 (C, FP64)",
+            "sample": f"{done} random simplices of {m} ({pieces} of {total_pieces} pieces, {t_run:.1f} s), "
+                      f"setup {setup:.2f} s; cells/s = sites / (setup + sample time / piece share)"}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    """Reference arm: the CPU oracle as it stands, on the host cores.  Each step
+    computes every piece of a random sample of the workload's sites, sized so that
+    the whole run stays within a few minutes; ms_per_step is that step's time."""
     if rank != 0:
         return
+    import numpy as np
+
+    import oracle as O
     from paper_2509_07175_b300 import inputs as I
 
     w = I.workload(args.workload)
-    base = cpu_baseline(w, budget_s=min(10.0, max(2.0, 60.0 / max(1, args.steps + args.warmup))))
-    line = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * len(w["sites"]) / base["value"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "desc": DESC.get(args.workload), "n_sites": len(w["sites"]),
-                       "n_simplices": len(w["simp"])},
+    n = len(w["sites"])
+    cores = os.cpu_count() or 1
+    o = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"], nthreads=cores)
+    rng = np.random.default_rng(0)
+    step_s = min(10.0, max(1.0, 90.0 / max(1, args.steps + args.warmup)))
+    pilot = rng.choice(n, min(n, 16 * cores), replace=False)
+    t0 = time.perf_counter()
+    o.site_pieces(pilot)
+    dp = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(n, max(len(pilot), len(pilot) * step_s / dp)))
+    times = []
+    for step in range(args.warmup + args.steps):
+        pick = rng.choice(n, k, replace=False)
+        t0 = time.perf_counter()
+        o.site_pieces(pick)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    o.close()
+    ms = 1e3 * statistics.median(times)
+    value = k / (ms / 1e3)
+    base = {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"each step: all pieces of {k} random sites of the {n} ({ms / 1e3:.2f} s)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": DESC.get(args.workload), "n_sites": n,
+                       "n_simplices": len(w["simp"]), "sites_per_step": k},
             "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -240,7 +366,7 @@ def main():
         # the learned proposal's network, trained on the GPU on labels the method
         # produces for seeded 100k-site cube instances (outside the timed region)
         from paper_2509_07175_b300 import learned as L
-        training = L.trained_state()
+        training = L.trained_state(mix=L.MIX)
     w = I.workload(args.workload, seed=replica_seed(rank))
     n = len(w["sites"])
     d = B.diagram_from_workload(w)
@@ -249,6 +375,24 @@ def main():
     prop = B.PROPOSAL_MLP if mlp else B.PROPOSAL_DISTANCE
     split = int(args.split == "on" and w["mode"] == B.MODE_3D and w.get("box") is None)
     form = dict(learned=0 if args.plain else 1, topk=args.topk, proposal=prop, split=split)
+    relax = None
+    if w.get("lloyd"):
+        # blue noise (Sec. 6.4): relax the sites by graph-captured Lloyd iterations
+        # of the timed form first; the iterations are timed as a whole
+        d.set_options(mapping=0, **form)
+        d.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.lloyd(int(w["lloyd"]), use_graph=True)
+        torch.cuda.synchronize()
+        relax = {"iters": int(w["lloyd"]), "s": time.perf_counter() - t0,
+                 "note": "graph-captured Lloyd iterations (compute + centroid update) from the white-noise sites, "
+                         "list size and mapping tuned on the white-noise sites"}
+        w = dict(w, sites=d.sites().double().cpu().numpy())
+        d.close()
+        d = B.diagram_from_workload(w)
+        if mlp:
+            L.load_state(d, training["state"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
@@ -273,9 +417,20 @@ def main():
     # the plain form (the paper's search alone) and the learned form with the
     # distance ranking beside the headline form: identical output, timed the same way
     beside = {}
+    network = None
     if not args.plain:
         d.set_options(learned=0, split=split)
         ref = d.compute()
+        if mlp:
+            # what the network ranks on this workload: recall of the neighbours among
+            # its top k of the 32 nearest, against the ranking by distance
+            x, yv = d.mlp_features()
+            z = d.mlp_forward(x)
+            zd = -torch.arange(32, device="cuda", dtype=torch.float32).expand(x.shape[0], 32)
+            network = {"recall_at_k": {str(k): {"network": L.recall_at_k(z, yv, k),
+                                                "distance": L.recall_at_k(zd, yv, k)} for k in (4, 8, 16, 24)},
+                       "rows": int(x.shape[0])}
+            del x, yv, z, zd
         nb = max(1, min(5, args.steps))
         beside["plain"] = time_form(dict(learned=0, split=split), nb)
         if mlp:
@@ -369,6 +524,8 @@ def main():
     flops = 8.0 * (counts["sites_scanned"] + 32 * counts.get("list_tests", 0))
     clip_s = statistics.median(clip_ms) / 1e3 if clip_ms else float("nan")
     achieved = flops / clip_s / 1e12
+    nnz_all = int(rs["nbr_off"][-1].item())
+    hbm_bytes = 16.0 * n + 4.0 * n + 12.0 * n + 8.0 * (n + 1) + 4.0 * nnz_all
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -381,7 +538,16 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_flood<float, 3D> (Alg. 3 clip + flood)", "bound": "alu", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "peak_source": f"{sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                     "peak_source": f"{sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",
+                     "limiter": "latency (dependent shared-memory, warp-vote and L2 chains at 12 warps per SM); "
+                                "neither roof is approached",
+                     "hbm": {"achieved": (hbm_bytes / clip_s / 1e9) if hbm_bytes else None,
+                             "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                             "frac": (hbm_bytes / clip_s / 1e9 / peaks["hbm_gbs"])
+                             if hbm_bytes and peaks.get("hbm_gbs") else None,
+                             "bytes": hbm_bytes, "note": "algorithmic bytes per launch: 100 B per cell x sites "
+                                                         "(site read 16, measure 4, centroid 12, CSR offset 8, "
+                                                         "neighbour ids 4 x degree)"},
                      "flops_per_launch": flops, "clip_ms": clip_s * 1e3,
                      "clip_share": (clip_s * 1e3) / (total_ms / args.steps),
                      "traffic": flood_traffic(args.workload),
@@ -409,9 +575,22 @@ def main():
                             "lr": training["lr"], "train_s": training["train_s"], "data_s": training["data_s"],
                             "loss_first_epoch": training["epoch_loss"][0],
                             "loss_last_epoch": training["epoch_loss"][-1],
-                            "data": "labels from plain computes of 8 seeded 100k-site unit-cube instances"}
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+                            "data": "labels from plain computes of seeded 100k-site instances: "
+                                    + ", ".join(f"{c} {nm}" for nm, c in L.MIX)}
+        if network is not None:
+            line["network"] = network
+    if relax is not None:
+        line["lloyd_relaxation"] = relax
+    if world == 1 and not args.no_cpu_baseline and relax is not None:
+        line["cpu_baseline"] = {"value": None, "reason": "the relaxed sites come from this library's own Lloyd "
+                                                         "iterations; the oracle is not fed from the CUDA path "
+                                                         "(blue100k checks blue noise against it)"}
+    elif world == 1 and not args.no_cpu_baseline:
+        base, op = cpu_baseline(w)
+        line["cpu_baseline"] = base
+        line["oracle_check"] = oracle_errors(w, rs, op)
+        line["serial_baseline"] = serial_baseline(w, total_pieces=int((op.meas > 0).sum()))
+        del op
     d.close()
     print(json.dumps(line), flush=True)
     if dist:

@@ -189,6 +189,26 @@ int vd_create(vd_ctx** out, const void* sites, int64_t n, int dim, int dtype);
  * VD_ERR_ARG for a weight that is not finite. */
 int vd_create_power2d(vd_ctx** out, const float* xy, const float* w, int64_t n);
 
+/* Power diagram in 3D or on a surface (the paper's extension to power diagrams
+ * by lifting, Sec. 6.3): the power distance of x to site i is
+ * |x - v_i|^2 - w_i.  Every site is lifted to (v_i, h_i) one dimension up,
+ * h_i = sqrt(eta - w_i) with eta = max_i w_i (found on the device); the domain
+ * lies at height 0, where |x - (v_i, h_i)|^2 = |x - v_i|^2 - w_i + eta, so the
+ * clipped (restricted) Voronoi diagram of the lifted sites is the power
+ * diagram.  Alg. 3 runs on the lifted sites: corners are tested against the
+ * lifted sites, the virtual edge goes from (v_i, h_i) to the corner, and the
+ * bisector planes are the power bisectors |w|^2 + h_j^2 - h_i^2 = 2 w.x
+ * (w = v_j - v_i; the float64 sign tests use the same h).  The weights realised
+ * are exactly eta - h_i^2 for the float h_i, i.e. w_i up to the rounding of h_i.
+ * w: device float [n], copied; NULL returns to the Voronoi diagram.  Power cells
+ * may be empty (a dominated site) or not contain their site.  The learned form's
+ * nearest lists, the split and the thread-per-pair mapping are not used while
+ * weights are set (the plain search, one warp per pair, per-simplex pieces).
+ * FP32 contexts with dim = 3 (tetrahedra, surface triangles or vd_set_box);
+ * planar diagrams use vd_create_power2d.  VD_ERR_ARG for another context or a
+ * weight that is not finite.  Synchronises the context stream. */
+int vd_set_weights(vd_ctx* ctx, const float* w);
+
 /* Set the domain M = {T_a} (Sec. 2.1).  verts: device pointer, nv*dim elements of
  * the context dtype; simplices: device pointer, m*simplex_verts int32 vertex
  * indices (3: triangles, 4: tetrahedra).  Copied and validated (indices in
@@ -263,7 +283,8 @@ int vd_get_result(vd_ctx* ctx, vd_result* out);
 /* Autotune the clip kernel now on the current sites (batching, Sec. 4.3: one
  * persistent launch drains the pair queue): runs vd_compute's work once per
  * candidate -- one warp or one thread per pair (3D FP32 tetrahedra without the
- * split), queue chunk 1, 2, 4, 8 or 16 (or vd_options.chunk alone when set) --
+ * split), queue chunk 1, 2, 4, 8 or 16 (or vd_options.chunk alone when set; the
+ * thread mapping's chunks beyond 1 only when its chunk 1 beat every warp one) --
  * times the clip phase with CUDA events and caches the fastest for mapping 0.
  * In the learned form with vd_options.nearest = 0 it first compares lists of
  * the 32 and of the 64 nearest (warp per pair, chunk 1) on the time of the
@@ -285,9 +306,12 @@ int vd_autotune(vd_ctx* ctx, int* mapping, int* chunk, float* times_ms);
 int vd_copy_result_host(vd_ctx* ctx, void* measure, void* centroid, int64_t* nbr_off, int32_t* nbr_idx);
 
 /* Lloyd's method (Sec. 6.4, density 1): iters times { compute the diagram;
- * v_i <- centroid_i (sites with empty cells stay) }.  use_graph = 1 captures one
- * iteration in a CUDA graph and replays it; the host reads the status once at
- * the end.  The last iteration's diagram is not recomputed for the final sites. */
+ * v_i <- centroid_i (sites with empty cells stay) }.  use_graph = 1 captures
+ * min(iters, 10) whole iterations in one CUDA graph (cached while that count,
+ * the options and the domain stay the same) and replays it, the remaining
+ * iters % 10 running as ordinary launches on the same stream; the host reads
+ * the status once at the end.  The last iteration's diagram is not recomputed
+ * for the final sites. */
 int vd_lloyd(vd_ctx* ctx, int iters, int use_graph);
 
 /* Copy the current site coordinates V (Sec. 2.1; after vd_lloyd, the relaxed

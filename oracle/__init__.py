@@ -171,6 +171,12 @@ class Oracle:
     def enumerate(self):
         return self._wrap(_load().orc_enumerate(self._h))
 
+    def all_sites(self):
+        """Every non-empty piece of every site: the per-site form over all sites
+        (parallel over sites; the same pieces as enumerate(), which works simplex
+        by simplex -- see tests/test_oracle_pins.py)"""
+        return self.site_pieces(np.arange(len(self.sites)))
+
     def site_pieces(self, sites):
         s = np.ascontiguousarray(sites, dtype=np.int64)
         return self._wrap(_load().orc_site_pieces(self._h, len(s), _ptr(s)))

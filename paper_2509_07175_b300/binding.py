@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "vd_autotune": ([P, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
         "vd_set_box": ([P, P, P], I),
         "vd_create_power2d": ([ctypes.POINTER(P), P, P, I64], I),
+        "vd_set_weights": ([P, P], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -116,7 +117,7 @@ def exported_symbols():
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
             "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box",
             "vd_create_power2d", "vd_compute_async", "vd_get_status", "vd_get_result", "vd_model_save",
-            "vd_model_load"]
+            "vd_model_load", "vd_set_weights"]
 
 
 class _DevArray:
@@ -209,6 +210,14 @@ class Diagram:
         for k, v in kw.items():
             setattr(o, k, v)
         _check(load().vd_set_options(self._h, ctypes.byref(o)), "vd_set_options")
+
+    def set_weights(self, weights):
+        """Power diagram (3D or surface): site weights (n,) float32, None for the Voronoi diagram."""
+        if weights is None:
+            _check(load().vd_set_weights(self._h, None), "vd_set_weights")
+            return
+        wt = weights.to(device="cuda", dtype=torch.float32).contiguous()
+        _check(load().vd_set_weights(self._h, wt.data_ptr()), "vd_set_weights")
 
     def update_sites(self, sites):
         s = sites.to(self.dtype).contiguous()

@@ -32,6 +32,7 @@ constexpr int MLP_RANK_BLOCKS = 3;    // inference blocks per SM (61 KB of share
 constexpr int TUNE_CHUNKS = 5;        // queue chunks the autotuner tries per mapping
 constexpr int kTuneChunks[TUNE_CHUNKS] = {1, 2, 4, 8, 16};
 constexpr int MLP_MAX_EPOCHS = 1024;  // per-epoch loss slots of vd_mlp_train
+constexpr int kLloydGraphIters = 10;  // Lloyd iterations captured in one graph
 
 }  // namespace
 
@@ -126,7 +127,13 @@ struct vd_ctx {
   unsigned long long last_stats[VD_STAT_N] = {0};
   bool computed = false;
   bool pending = false;        // vd_compute_async enqueued work whose status is not read yet
+  // power diagram (vd_set_weights): lift h_i of every site, its maximum, on / off
+  float* lift = nullptr;
+  int* lift_scratch = nullptr;  // [3]: ordered max weight, ordered max lift, bad-weight flag
+  float lift_max = 0.f;
+  bool lift_on = false;
   cudaGraphExec_t gexec = nullptr;
+  int graph_iters = 0;         // Lloyd iterations held by the captured graph
   cudaGraph_t graph = nullptr;
   cudaEvent_t ev[VD_PHASE_N + 1] = {};
   bool timing_now = false;     // events recorded by the current enqueue
@@ -196,8 +203,12 @@ static void free_domain(vd_ctx* c) {
 // device context view
 // ---------------------------------------------------------------------------
 static bool split_active(const vd_ctx* c) {
-  return c->opt.split && c->split_ok && !c->box && c->mode == VD_MODE_3D && c->dtype == VD_F32;
+  // power cells need not contain their sites: the split's premise does not hold
+  return c->opt.split && c->split_ok && !c->box && c->mode == VD_MODE_3D && c->dtype == VD_F32 && !c->lift_on;
 }
+
+// the learned form's nearest lists (3D distances; power diagrams run the plain search)
+static bool lists_active(const vd_ctx* c) { return c->opt.learned && !c->cand && !c->lift_on; }
 
 template <typename T>
 static Dev<T> make_dev(vd_ctx* c) {
@@ -221,7 +232,9 @@ static Dev<T> make_dev(vd_ctx* c) {
   }
   if (c->cand) { D.cand = c->cand; D.ncand = c->ncand; }
   else { D.cand = nullptr; D.ncand = 0; }
-  D.knn = (c->opt.learned && !c->cand) ? c->knn : nullptr;
+  D.knn = lists_active(c) ? c->knn : nullptr;
+  D.lift = c->lift_on ? c->lift : nullptr;
+  D.lift_max = c->lift_on ? c->lift_max : 0.f;
   D.knn_d2 = c->knn_d2;
   D.knn2 = (D.knn && c->cur_list64) ? c->knn2 : nullptr;
   D.knn_r64 = c->knn_r64;
@@ -302,12 +315,12 @@ static void enqueue_compute(vd_ctx* c) {
   }
   mark(c, 1);
   // learned form (FP32): the 32-nearest pass also yields delta_i
-  const bool fused = c->opt.learned && !c->cand && std::is_same<T, float>::value;
+  const bool fused = lists_active(c) && std::is_same<T, float>::value;
   if (!fused) {
     k_delta<T><<<nblk(c->n, 128), 128, 0, s>>>(D, (T*)c->delta);
     c->launches += 1;
   }
-  if (c->opt.learned && !c->cand) {
+  if (lists_active(c)) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
     k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, fused ? (T*)c->delta : nullptr,
                                                      c->cur_list64 ? c->knn2 : nullptr, c->knn_r64);
@@ -362,10 +375,19 @@ static void enqueue_compute(vd_ctx* c) {
     if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value)
       k_flood_thread<<<c->flood_grid_t, FLOOD_T_THREADS, 0, s>>>(D, c->cur_chunk);
   } else {
-    if (D.knn2)
+    bool power = false;
+    if constexpr (std::is_same<T, float>::value && MODE != VD_MODE_2D) {
+      if (D.lift) {
+        k_flood<T, MODE, false, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+        power = true;
+      }
+    }
+    if (power) {
+    } else if (D.knn2) {
       k_flood<T, MODE, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
-    else
+    } else {
       k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+    }
   }
   c->launches += 1;
   mark(c, 4);
@@ -420,6 +442,14 @@ static int flood_config(vd_ctx* c) {
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_flood<T, MODE, true>, FLOOD_WARPS * 32,
                                                    c->flood_smem));
   per_sm = std::min(per_sm, per_sm_x);
+  if constexpr (std::is_same<T, float>::value && MODE != VD_MODE_2D) {
+    int per_sm_p = 0;
+    CK(cudaFuncSetAttribute(k_flood<T, MODE, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->flood_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, k_flood<T, MODE, false, true>, FLOOD_WARPS * 32,
+                                                     c->flood_smem));
+    per_sm = std::min(per_sm, per_sm_p);
+  }
   c->flood_grid = std::max(1, per_sm) * c->nsm;
   int per_sm_k = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_k, k_knn<T>, KNN_WARPS * 32, 0));
@@ -448,7 +478,7 @@ static int flood_config(vd_ctx* c) {
 // learned form: whether the lists carry the 64 nearest (the caller's choice, else
 // the autotuned one, 64 until tuned)
 static bool list64_choice(const vd_ctx* c) {
-  if (!c->opt.learned || c->cand) return false;
+  if (!lists_active(c)) return false;
   if (c->opt.nearest == 32) return false;
   if (c->opt.nearest == 64) return true;
   return c->tuned ? c->tuned_list64 : true;
@@ -462,7 +492,7 @@ static void resolve_mapping(vd_ctx* c) {
     m = c->tuned ? c->tuned_mapping : 1;
     if (ch <= 0) ch = c->tuned ? c->tuned_chunk : 1;
   }
-  if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c))) m = 1;  // thread per pair: 3D FP32 tetrahedra only
+  if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c) || c->lift_on)) m = 1;  // thread per pair: 3D FP32 tetrahedra only
   c->cur_mapping = m;
   c->cur_list64 = list64_choice(c);
   c->cur_chunk = std::max(1, std::min(ch <= 0 ? 1 : ch, 64));
@@ -640,6 +670,42 @@ int vd_create_power2d(vd_ctx** out, const float* xy, const float* w, int64_t n) 
   cudaFree(lifted);
   cudaFree(scratch);
   return rc;
+}
+
+int vd_set_weights(vd_ctx* c, const float* w) {
+  if (!c) return VD_ERR_ARG;
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  c->tuned = false;
+  c->sites_fresh = c->knn_fresh = false;
+  if (!w) { c->lift_on = false; return VD_OK; }
+  if (c->dtype != VD_F32 || c->dim != 3) return VD_ERR_ARG;
+  if (!c->lift) {
+    DALLOC(c->lift, float, c->n, false);
+    DALLOC(c->lift_scratch, int, 3, false);
+  }
+  cudaStream_t s = c->stream;
+  // ordered bits of -3e38 (weights' maximum starts below any finite weight), of 0
+  // (the lifts' maximum), and the bad-weight flag
+  int init[3] = {(int)0x80000000 ^ 0x7fffffff, 0, 0};
+  {
+    float lo = -3.0e38f;
+    int b;
+    std::memcpy(&b, &lo, 4);
+    init[0] = b >= 0 ? b : b ^ 0x7fffffff;
+  }
+  CK(cudaMemcpyAsync(c->lift_scratch, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  k_power_max<<<std::max(1u, std::min(nblk(c->n, 256), 1024u)), 256, 0, s>>>(w, c->n, c->lift_scratch);
+  k_power_heights<<<nblk(c->n, 256), 256, 0, s>>>(w, c->n, c->lift_scratch, c->lift, c->lift_scratch + 2);
+  CK(cudaGetLastError());
+  int back[3];
+  CK(cudaMemcpyAsync(back, c->lift_scratch, sizeof(back), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (back[2]) { c->lift_on = false; return VD_ERR_ARG; }
+  int b = back[1] >= 0 ? back[1] : back[1] ^ 0x7fffffff;
+  std::memcpy(&c->lift_max, &b, 4);
+  c->lift_on = true;
+  return VD_OK;
 }
 
 int vd_update_sites(vd_ctx* c, const void* sites) {
@@ -953,7 +1019,7 @@ int vd_set_domain(vd_ctx* c, const void* verts, int64_t nv, const int32_t* simpl
 }
 
 static bool wants_network(const vd_ctx* c) {
-  return c->opt.learned && !c->cand && c->opt.proposal == VD_PROPOSAL_MLP;
+  return lists_active(c) && c->opt.proposal == VD_PROPOSAL_MLP;
 }
 
 // Autotuner of the clip kernel's mapping: runs the whole compute on the current
@@ -965,7 +1031,7 @@ static int autotune(vd_ctx* c) {
   // in tune_ms: (mapping - 1) * TUNE_CHUNKS + index of the chunk
   int cand_m[2 * TUNE_CHUNKS], cand_c[2 * TUNE_CHUNKS], cand_s[2 * TUNE_CHUNKS], nc = 0;
   for (int m = 1; m <= 2; ++m) {
-    if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c))) continue;
+    if (m == 2 && (c->flood_grid_t == 0 || c->box || split_active(c) || c->lift_on)) continue;
     for (int k = 0; k < TUNE_CHUNKS; ++k) {
       int ch = c->opt.chunk > 0 ? std::min(c->opt.chunk, 64) : kTuneChunks[k];
       cand_m[nc] = m; cand_c[nc] = ch; cand_s[nc++] = (m - 1) * TUNE_CHUNKS + k;
@@ -983,7 +1049,7 @@ static int autotune(vd_ctx* c) {
   // (the list pass, the seeding and the clip) with one warp per pair, chunk 1
   c->tune_list_ms[0] = c->tune_list_ms[1] = -1.f;
   bool list64 = list64_choice(c);
-  if (c->opt.learned && !c->cand && c->opt.nearest == 0) {
+  if (lists_active(c) && c->opt.nearest == 0) {
     for (int e = 0; e < 2; ++e) {
       c->cur_mapping = 1;
       c->cur_chunk = 1;
@@ -1005,7 +1071,10 @@ static int autotune(vd_ctx* c) {
   int best = 0;
   double best_ms = 1e300;
   for (int k = 0; k < 2 * TUNE_CHUNKS; ++k) c->tune_ms[k] = -1.f;
+  double best_warp = 1e300, thread1 = -1.0;
   for (int k = 0; k < nc; ++k) {
+    // the thread mapping at other chunks only if its first chunk beat every warp candidate
+    if (cand_m[k] == 2 && cand_c[k] != 1 && thread1 >= 0 && thread1 >= best_warp) continue;
     c->cur_mapping = cand_m[k];
     c->cur_chunk = cand_c[k];
     CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
@@ -1018,10 +1087,12 @@ static int autotune(vd_ctx* c) {
     if (st) return st;
     double ms = c->last_phase_ms[VD_PHASE_CLIP];
     if (cand_s[k] >= 0) c->tune_ms[cand_s[k]] = (float)ms;
+    if (cand_m[k] == 1) best_warp = std::min(best_warp, ms);
+    else if (cand_c[k] == 1) thread1 = ms;
     if (ms < best_ms) { best_ms = ms; best = k; }
   }
   c->sites_fresh = true;
-  c->knn_fresh = c->opt.learned && !c->cand;
+  c->knn_fresh = lists_active(c);
   c->tuned = true;
   c->tuned_mapping = cand_m[best];
   c->tuned_chunk = cand_c[best];
@@ -1082,7 +1153,7 @@ int vd_compute(vd_ctx* c, vd_result* out) {
   c->timing_now = false;
   c->pending = false;
   c->sites_fresh = true;
-  c->knn_fresh = c->opt.learned && !c->cand;
+  c->knn_fresh = lists_active(c);
   fill_result(c, out);
   return st;
 }
@@ -1099,7 +1170,7 @@ int vd_compute_async(vd_ctx* c) {
   CK(cudaGetLastError());
   c->pending = true;
   c->sites_fresh = true;
-  c->knn_fresh = c->opt.learned && !c->cand;
+  c->knn_fresh = lists_active(c);
   return VD_OK;
 }
 
@@ -1159,6 +1230,13 @@ int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
   c->sites_fresh = c->knn_fresh = false;
   CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
   if (use_graph) {
+    // one graph holds up to kLloydGraphIters whole iterations (compute + update);
+    // it is replayed iters / k times and the rest runs eagerly on the same stream
+    const int k = std::min(iters, kLloydGraphIters);
+    if (c->gexec && c->graph_iters != k) {
+      cudaGraphExecDestroy(c->gexec); c->gexec = nullptr;
+      cudaGraphDestroy(c->graph); c->graph = nullptr;
+    }
     if (!c->gexec) {
       cudaStream_t cap = c->stream;
       if (!cap) {
@@ -1169,18 +1247,30 @@ int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
       CK(cudaStreamSynchronize(saved));
       c->stream = cap;
       CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      enqueue_any(c);
-      enqueue_lloyd(c);
+      for (int t = 0; t < k; ++t) {
+        enqueue_any(c);
+        enqueue_lloyd(c);
+      }
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cap, &g);
       c->stream = saved;
       if (e != cudaSuccess) return VD_ERR_CUDA;
       c->graph = g;
+      c->graph_iters = k;
       CK(cudaGraphInstantiate(&c->gexec, g, 0));
     }
     cudaStream_t run = c->stream ? c->stream : c->own_stream;
     if (run != c->stream) { CK(cudaStreamSynchronize(c->stream)); }
-    for (int t = 0; t < iters; ++t) CK(cudaGraphLaunch(c->gexec, run));
+    for (int t = 0; t < iters / k; ++t) CK(cudaGraphLaunch(c->gexec, run));
+    if (iters % k) {
+      cudaStream_t saved = c->stream;
+      c->stream = run;
+      for (int t = 0; t < iters % k; ++t) {
+        enqueue_any(c);
+        enqueue_lloyd(c);
+      }
+      c->stream = saved;
+    }
     if (run != c->stream) { CK(cudaStreamSynchronize(run)); }
   } else {
     for (int t = 0; t < iters; ++t) {
@@ -1534,7 +1624,7 @@ int vd_mlp_forward(vd_ctx* c, const void* x, int64_t rows, float* logits) {
 
 int vd_get_candidate_masks(vd_ctx* c, uint32_t* masks) {
   if (!c || !masks) return VD_ERR_ARG;
-  if (!c->computed || !c->sites_fresh || !c->knn_fresh || !c->opt.learned || c->cand) return VD_ERR_STATE;
+  if (!c->computed || !c->sites_fresh || !c->knn_fresh || !lists_active(c)) return VD_ERR_STATE;
   CK(cudaMemcpyAsync(masks, c->cmask, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, c->stream));
   return VD_OK;
 }

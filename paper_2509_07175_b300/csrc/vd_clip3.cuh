@@ -13,6 +13,12 @@
 // Geometry is FP32 in the frame of v_i.  Every corner carries a bound on the
 // error of its coordinates; side tests that do not clear their bound are
 // settled by the float64 predicate on the defining planes (vd_common.cuh).
+//
+// The helpers run on every clip (search, clip, integration, nearest-site query)
+// are inlined into the pair loop: as out-of-line calls each paid a save and a
+// restore of its registers through local memory (10-12 % of the kernel's time
+// on the shell, the 100k cube and the 5M box).  Only the float64 paths, which
+// run for a few per cent of the decisions, stay out of line.
 #pragma once
 
 #include "vd_dev.cuh"
@@ -34,6 +40,7 @@ struct Warp3 {
   uchar4 tn[MAXT];      // neighbour corners across dual edges x->y, y->z, z->x
   float4 tq[MAXT];      // corner coordinates (frame of v_i), w = coordinate error bound
   int twit[MAXT];       // certified closer site of an outside corner
+  mutable int tied;     // this pair met an exact tie or an uncertain sign (see process_pair)
   int stri[MAXP], etri[MAXP];  // boundary loop: new corner starting / ending at a plane
   int pref[MAXP];       // reference corner of each face (integration)
   float parea[MAXP][3]; // face vector areas
@@ -129,7 +136,12 @@ __device__ __noinline__ ePlane eplane(const Dev<float>& C, int a, int i, int src
   if (src >= 0) {
     ed3 vj{mk(C.sites[3 * src]), mk(C.sites[3 * src + 1]), mk(C.sites[3 * src + 2])};
     p.n = sub3(vj, vi);
-    p.c = half(dot3(p.n, p.n));
+    ed w2 = dot3(p.n, p.n);
+    if (C.lift) {  // power bisector: (|v_j - v_i|^2 + h_j^2 - h_i^2) / 2
+      ed hj = mk(C.lift[src]), hi = mk(C.lift[i]);
+      w2 = w2 + (hj * hj - hi * hi);
+    }
+    p.c = half(w2);
     return p;
   }
   int f = -1 - src, l0, l1, l2;
@@ -202,7 +214,7 @@ __device__ __noinline__ float4 refine64(const Dev<float>& C, int a, int i, int s
 }
 
 // ----- exact side tests ----------------------------------------------------------
-__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4) {
+__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4, bool mark = false) {
   ePlane p[4];
   uchar4 v = W.tv[t];
   // the corner lies on each of its own planes: the side value is exactly zero
@@ -215,6 +227,7 @@ __device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int 
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
+    if (mark) W.tied = 1;  // a clip decision met a tie: positivity from the measures
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, W.psrc[v.x], W.psrc[v.y], W.psrc[v.z], src4, tie, 0);
   }
@@ -233,7 +246,7 @@ __device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int 
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return exact_side(C, W, a, i, t, W.psrc[pl]);
+  return exact_side(C, W, a, i, t, W.psrc[pl], true);
 }
 
 // ----- one pair ------------------------------------------------------------------
@@ -248,12 +261,13 @@ __device__ __forceinline__ void add_plane(Warp3& W, int slot, float4 P, float2 M
   __syncwarp();
 }
 
-// nearest site through the warp (counted)
-__device__ __noinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, float y, float z, int lane,
-                                     Counters& K) {
+// nearest site through the warp (counted); POW: of the lifted point (x, y, z, u)
+template <bool POW = false>
+__device__ __forceinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, float y, float z, int lane,
+                                        Counters& K, float u = 0.f) {
   float d2;
   int sc = 0;
-  int k = warp_nearest(C.G, x, y, z, lane, W.S, d2, &sc);
+  int k = warp_nearest<float, POW>(C.G, x, y, z, lane, W.S, d2, &sc, C.lift, u);
   K.nn++;
   K.scanned += sc;
   return k;
@@ -264,8 +278,9 @@ __device__ __noinline__ int nn_query(const Dev<float>& C, Warp3& W, float x, flo
 // to the point as v_i lies within 2|s| of v_i), found with no grid scan.
 template <typename NL>
 __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const NL& L, int i, float3 vi,
-                                         float sx, float sy, float sz, int lane, Counters& K) {
+                                         float sx, float sy, float sz, int lane, Counters& K, float su = 0.f) {
   float px = vi.x + sx, py = vi.y + sy, pz = vi.z + sz;
+  if (NL::pow) return nn_query<true>(C, W, px, py, pz, lane, K, su);
   if (L.r32 > 0.f) {
     float s = sqrtf(sx * sx + sy * sy + sz * sz);
     if (2.f * s * (1.f + 1e-5f) + 4e-7f * (fabsf(px) + fabsf(py) + fabsf(pz)) <= L.r32) {
@@ -308,7 +323,7 @@ __device__ __forceinline__ int nn_search(const Dev<float>& C, Warp3& W, const NL
       return kk;
     }
   }
-  return nn_query(C, W, px, py, pz, lane, K);
+  return nn_query<false>(C, W, px, py, pz, lane, K);
 }
 
 // Coordinates of site k (warp-uniform k >= 0): shuffled from the lane whose
@@ -332,13 +347,16 @@ __device__ __forceinline__ void listed_coords(const Dev<float>& C, const NL& L, 
 // Sec. 3.2 with the start point of Sec. 5.1 (and the learned shortcut).
 // Returns the bisector site j for the outside corner t.
 template <typename NL>
-__device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, const NL& L, int i, float3 vi,
+__device__ __forceinline__ int find_bisector(const Dev<float>& C, Warp3& W, const NL& L, int i, float3 vi,
                                           int t, int lane, Counters& K) {
   float4 q = W.tq[t];
   int wit = W.twit[t];
-  float dist = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
-  float dx = q.x / dist, dy = q.y / dist, dz = q.z / dist;
-  float gx = q.x, gy = q.y, gz = q.z;
+  // power diagram: the virtual edge runs from the lifted site (v_i, h_i) to the
+  // corner (p, 0); gu is its lifted component (relative to h_i), 0 otherwise
+  const float hi = NL::pow ? (float)L.hi : 0.f;
+  float dist = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + hi * hi);
+  float dx = q.x / dist, dy = q.y / dist, dz = q.z / dist, du = -hi / dist;
+  float gx = q.x, gy = q.y, gz = q.z, gu = -hi;
   int j = wit;
   float delta = C.delta[i];
   if (__any_sync(FULL, L.cand)) {
@@ -378,24 +396,25 @@ __device__ __noinline__ int find_bisector(const Dev<float>& C, Warp3& W, const N
   for (int lam = 2; lam < 2 + C.max_lambda; ++lam) {
     float step = (float)lam * delta;
     if (!(step < dist)) break;
-    float sx = dx * step, sy = dy * step, sz = dz * step;
-    int k = nn_query(C, W, vi.x + sx, vi.y + sy, vi.z + sz, lane, K);
+    float sx = dx * step, sy = dy * step, sz = dz * step, su = du * step;
+    int k = nn_query<NL::pow>(C, W, vi.x + sx, vi.y + sy, vi.z + sz, lane, K, hi + su);
     K.lam++;
-    if (k != i) { gx = sx; gy = sy; gz = sz; j = k; break; }
+    if (k != i) { gx = sx; gy = sy; gz = sz; gu = su; j = k; break; }
   }
 search:
   for (int s = 0; s < C.max_search; ++s) {
     float wx = C.sites[3 * j] - vi.x, wy = C.sites[3 * j + 1] - vi.y, wz = C.sites[3 * j + 2] - vi.z;
-    float den = wx * gx + wy * gy + wz * gz;
+    float wu = NL::pow ? C.lift[j] - hi : 0.f;  // the lifted sites' difference
+    float den = wx * gx + wy * gy + wz * gz + wu * gu;
     if (!(den > 0.f)) { K.fallback++; return wit; }
-    float tt = 0.5f * (wx * wx + wy * wy + wz * wz) / den;
+    float tt = 0.5f * (wx * wx + wy * wy + wz * wz + wu * wu) / den;
     if (!(tt < 1.f)) return j;   // the bisector meets the segment at its end
-    float sx = gx * tt, sy = gy * tt, sz = gz * tt;
-    int k = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K);
+    float sx = gx * tt, sy = gy * tt, sz = gz * tt, su = gu * tt;
+    int k = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K, hi + su);
     K.search++;
     if (k == i || k == j) return j;
     j = k;
-    gx = sx; gy = sy; gz = sz;
+    gx = sx; gy = sy; gz = sz; gu = su;
   }
   K.fallback++;
   return wit;
@@ -403,7 +422,7 @@ search:
 
 // Clip by the plane in slot pl, removing the component of outside corners that
 // contains p.  Returns 0 (clipped), 1 (P became empty), -1 (error, status set).
-__device__ __noinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, int pl, int p, int lane) {
+__device__ __forceinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i, int pl, int p, int lane) {
   unsigned om[3], R[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -616,7 +635,7 @@ __device__ __forceinline__ float4 finish_moments(float sigma, float4 S, float4 O
 // reference corner of each face and the origin are the smallest-key corners, and
 // the terms are summed in corner-key order.  sigma is +-1 (orientation of the
 // dual mesh against space).
-__device__ __noinline__ void integrate(const Dev<float>& C, Warp3& W, const Masks& Mk, int a, int i, float3 vi,
+__device__ __forceinline__ void integrate(const Dev<float>& C, Warp3& W, const Masks& Mk, int a, int i, float3 vi,
                                        float sigma, int lane, float& vol, float3& m1) {
   for (int x = lane; x < MAXP; x += 32) {
     W.pref[x] = 0x7fffffff;
@@ -815,10 +834,18 @@ __device__ void init_tet(const Dev<float>& C, Warp3& W, Masks& Mk, int a, int i,
 #define PROF_ADD(k) do {} while (0)
 #endif
 
-template <bool EXT>
+template <bool EXT, bool POW = false>
 __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long long slot, int lane) {
   Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const NbrList<float, EXT> L = load_nbrs<float, EXT>(C, i, lane);
+  const NbrList<float, EXT, POW> L = load_nbrs<float, EXT, POW>(C, i, lane);
+  // power diagram: B_ij on u = 0 is n.x <= (|w|^2 + h_j^2 - h_i^2) / 2 (Sec. 6.3)
+  auto lifted = [&](int j, float4& P, float2& M) {
+    if (POW) {
+      float hj = C.lift[j], h = (float)L.hi;
+      P.w += 0.5f * (hj * hj - h * h);
+      M.y += 0.5f * (hj * hj + h * h);
+    }
+  };
   PROF_T0();
   float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   Masks Mk;
@@ -826,6 +853,8 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   // orientation of the dual mesh against space: with the corner table below, the
   // edge-term sum of integrate() has the sign of the tet's orientation
   const bool bx = box_pair(C, a);
+  if (lane == 0) W.tied = 0;
+  __syncwarp();
   float sigma = 1.f;  // the box's dual mesh is oriented like a positive tet
   if (!bx) {
     sigma = (float)C.tsgn[a];
@@ -879,6 +908,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       float jx, jy, jz;
       listed_coords(C, L, j, lane, jx, jy, jz);
       plane_bis_at(jx, jy, jz, vi, P, M);
+      lifted(j, P, M);
     }
     add_plane(W, pl, P, M, j, lane);
     if (side_of(C, W, a, i, p, pl) >= 0) {
@@ -886,6 +916,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       K.fallback++;
       j = W.twit[p];
       plane_bis(C, j, vi, P, M);
+      lifted(j, P, M);
       add_plane(W, pl, P, M, j, lane);
     }
     int rc = clip(C, W, Mk, a, i, pl, p, lane);
@@ -900,7 +931,18 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
   float vol = 0.f;
   float3 m1 = make_float3(0.f, 0.f, 0.f);
   if (!empty) integrate(C, W, Mk, a, i, vi, sigma, lane, vol, m1);
-  bool nonempty = !empty && vol > 0.f;
+  // Positive measure (Sec. 2.2) is decided from the exact structure: every side
+  // decision was certified, so with no exact tie (or uncertain sign) in this pair
+  // the piece (at least four corners) and each of its faces (at least three) has
+  // positive measure however FP32 rounds a face far below the cell's size (its
+  // corners can round to one point).  After a tie the computed measures decide.
+  __syncwarp();
+  const bool exact_faces = W.tied == 0;
+  bool nonempty = !empty && (vol > 0.f || exact_faces);
+  if (nonempty && !(vol > 0.f)) {  // a sliver below FP32 resolution: positive, negligible
+    vol = 1.17549435e-38f;
+    m1 = make_float3(0.f, 0.f, 0.f);
+  }
   // faces of positive area: output flags and propagate (Alg. 4 / Alg. 5 rules)
   int nflag = 0;
   int myflag[2];
@@ -910,7 +952,7 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
     int x = lane + 32 * h;
     if (nonempty && x < MAXP && ((Mk.palive >> x) & 1ull)) {
       float ax = W.parea[x][0], ay = W.parea[x][1], az = W.parea[x][2];
-      if (ax * ax + ay * ay + az * az > 0.f) {
+      if (exact_faces || ax * ax + ay * ay + az * az > 0.f) {
         int src = W.psrc[x];
         bis[h] = src >= 0;
         if (src >= 0) {

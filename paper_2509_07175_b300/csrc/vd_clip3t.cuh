@@ -35,6 +35,7 @@ struct Poly {
   unsigned tn[MAXT];   // neighbours across x->y, y->z, z->x, same packing
   float4 tq[MAXT];     // corner (frame of v_i), w = coordinate error bound
   int twit[MAXT];      // certified closer site of an outside corner
+  mutable int tied;    // this pair met an exact tie or an uncertain sign
 };
 
 struct Masks {
@@ -157,7 +158,7 @@ __device__ int t_nn_search(const Dev<float>& C, const TList& L, int i, float3 vi
 }
 
 // ----- exact side test -------------------------------------------------------------
-__device__ __noinline__ int t_exact_side(const Dev<float>& C, const Poly& P, int a, int i, int t, int src4) {
+__device__ __noinline__ int t_exact_side(const Dev<float>& C, const Poly& P, int a, int i, int t, int src4, bool mark = false) {
   unsigned v = P.tv[t];
   int s0 = P.psrc[b0(v)], s1 = P.psrc[b1(v)], s2 = P.psrc[b2(v)];
   if (src4 == s0 || src4 == s1 || src4 == s2) return 0;
@@ -170,6 +171,7 @@ __device__ __noinline__ int t_exact_side(const Dev<float>& C, const Poly& P, int
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
+    if (mark) P.tied = 1;  // a clip decision met a tie: positivity from the measures
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, s0, s1, s2, src4, tie, 0);
   }
@@ -187,7 +189,7 @@ __device__ __forceinline__ int t_side_of(const Dev<float>& C, const Poly& P, int
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return t_exact_side(C, P, a, i, t, P.psrc[pl]);
+  return t_exact_side(C, P, a, i, t, P.psrc[pl], true);
 }
 
 // ----- point-in-cell test of a corner (Sec. 3.1; same criterion as the warp form) ---
@@ -587,7 +589,8 @@ __device__ __noinline__ void t_integrate(const Dev<float>& C, Poly& P, const Mas
   for (int x = 0; x < MAXP; ++x)
     if ((Mk.palive >> x) & 1ull) {
       float ax = parea[x][0], ay = parea[x][1], az = parea[x][2];
-      if (ax * ax + ay * ay + az * az > 0.f) pa |= 1ull << x;
+      // exact structure without a tie: every alive plane is a face of positive area
+      if (!P.tied || ax * ax + ay * ay + az * az > 0.f) pa |= 1ull << x;
     }
   posarea = pa;
 }
@@ -619,6 +622,7 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
   float3 vi = make_float3(C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]);
   Masks Mk;
   t_init_tet(C, P, Mk, a, vi);
+  P.tied = 0;
   float sigma;
   {
     sigma = (float)C.tsgn[a];
@@ -669,7 +673,11 @@ __device__ void process_pair(const Dev<float>& C, Poly& P, int a, int i, long lo
   float3 m1 = make_float3(0.f, 0.f, 0.f);
   unsigned long long posarea = 0;
   if (!empty) t_integrate(C, P, Mk, a, i, vi, sigma, vol, m1, posarea);
-  bool nonempty = !empty && vol > 0.f;
+  bool nonempty = !empty && (vol > 0.f || !P.tied);
+  if (nonempty && !(vol > 0.f)) {  // a sliver below FP32 resolution (as in the warp form)
+    vol = 1.17549435e-38f;
+    m1 = make_float3(0.f, 0.f, 0.f);
+  }
   int nflag = nonempty ? __popcll(posarea) : 0;
   long long fbase = nflag ? (long long)atomicAdd(C.ctr + CTR_FLAGS, (unsigned long long)nflag) : 0;
   if (fbase + nflag > C.fcap) { set_error(C.status, VD_ERR_CAPACITY); return; }

@@ -34,6 +34,7 @@ struct WarpP {
   int ve[MAXV];    // plane of the edge from corner k to corner k+1
   int vst[MAXV];   // 0 untested, 1 inside, 2 outside
   int vwit[MAXV];
+  mutable int tied;  // this pair met an exact tie or an uncertain sign
   ScanScratch S;
   CornerScratch A;
 };
@@ -97,7 +98,12 @@ __device__ __noinline__ ePlane eplane(const Dev<T>& C, int a, int i, int src) {
   if (src >= 0) {
     ed3 vj{mk(C.sites[3 * src]), mk(C.sites[3 * src + 1]), mk(C.sites[3 * src + 2])};
     p.n = sub3(vj, vi);
-    p.c = half(dot3(p.n, p.n));
+    ed w2 = dot3(p.n, p.n);
+    if (C.lift) {  // power bisector: (|v_j - v_i|^2 + h_j^2 - h_i^2) / 2
+      ed hj = mk(C.lift[src]), hi = mk(C.lift[i]);
+      w2 = w2 + (hj * hj - hi * hi);
+    }
+    p.c = half(w2);
     return p;
   }
   const T *A = vtx(C, a, 0), *B = vtx(C, a, 1), *Cc = vtx(C, a, 2);
@@ -149,7 +155,7 @@ __device__ __noinline__ typename Prec<T>::V4 refine(const Dev<T>& C, const WarpP
 }
 
 template <typename T>
-__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4) {
+__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4, bool mark = false) {
   int km = (k + nv - 1) % nv;
   // the corner lies on each of its own planes: the side value is exactly zero
   if (src4 == -1 || src4 == W.psrc[W.ve[km]] || src4 == W.psrc[W.ve[k]]) return 0;
@@ -162,6 +168,7 @@ __device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
+    if (mark) W.tied = 1;  // a clip decision met a tie: positivity from the measures
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, -1, W.psrc[W.ve[km]], W.psrc[W.ve[k]], src4, tie, 0);
   }
@@ -178,18 +185,19 @@ __device__ __forceinline__ int side_of(const Dev<T>& C, const WarpP<T>& W, int a
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return exact_side(C, W, a, i, k, nv, W.psrc[pl]);
+  return exact_side(C, W, a, i, k, nv, W.psrc[pl], true);
 }
 
 struct Counters {
   unsigned long long nn, corner, clips, lam, search, scanned, fallback, learned, list;
 };
 
-template <typename T>
-__device__ __noinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z, int lane, Counters& K) {
+template <typename T, bool POW = false>
+__device__ __noinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z, int lane, Counters& K,
+                                     T u = T(0)) {
   T d2;
   int sc = 0;
-  int k = warp_nearest(C.G, x, y, z, lane, W.S, d2, &sc);
+  int k = warp_nearest<T, POW>(C.G, x, y, z, lane, W.S, d2, &sc, C.lift, u);
   K.nn++;
   K.scanned += sc;
   return k;
@@ -198,8 +206,9 @@ __device__ __noinline__ int nn_query(const Dev<T>& C, WarpP<T>& W, T x, T y, T z
 // nearest site of v_i + s; learned form: from the 32-NN list when 2|s| <= r32
 template <typename T, typename NL>
 __device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const NL& L, int i, const T* vi,
-                                         T sx, T sy, T sz, int lane, Counters& K) {
+                                         T sx, T sy, T sz, int lane, Counters& K, T su = T(0)) {
   T px = vi[0] + sx, py = vi[1] + sy, pz = vi[2] + sz;
+  if (NL::pow) return nn_query<T, true>(C, W, px, py, pz, lane, K, su);
   if (L.r32 > 0.f) {
     T s = sqrt(sx * sx + sy * sy + sz * sz);
     if ((float)(T(2) * s) * (1.f + 2e-5f) + 4e-7f * (float)(fabs(px) + fabs(py) + fabs(pz)) <= L.r32) {
@@ -243,7 +252,7 @@ __device__ __forceinline__ int nn_search(const Dev<T>& C, WarpP<T>& W, const NL&
       return kk;
     }
   }
-  return nn_query(C, W, px, py, pz, lane, K);
+  return nn_query<T, false>(C, W, px, py, pz, lane, K);
 }
 
 template <typename T, typename NL>
@@ -251,9 +260,11 @@ __device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, const NL
                                           int k, int lane, Counters& K) {
   typename Prec<T>::V4 q = W.vq[k];
   int wit = W.vwit[k];
-  T dist = sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
-  T dx = q.x / dist, dy = q.y / dist, dz = q.z / dist;
-  T gx = q.x, gy = q.y, gz = q.z;
+  // power diagram: the virtual edge from the lifted site (v_i, h_i) to (p, 0)
+  const T hi = NL::pow ? L.hi : T(0);
+  T dist = sqrt(q.x * q.x + q.y * q.y + q.z * q.z + hi * hi);
+  T dx = q.x / dist, dy = q.y / dist, dz = q.z / dist, du = -hi / dist;
+  T gx = q.x, gy = q.y, gz = q.z, gu = -hi;
   int j = wit;
   T delta = C.delta[i];
   if (__any_sync(FULL, L.cand)) {
@@ -288,24 +299,25 @@ __device__ __noinline__ int find_bisector(const Dev<T>& C, WarpP<T>& W, const NL
   for (int lam = 2; lam < 2 + C.max_lambda; ++lam) {
     T step = T(lam) * delta;
     if (!(step < dist)) break;
-    T sx = dx * step, sy = dy * step, sz = dz * step;
-    int kk = nn_query(C, W, vi[0] + sx, vi[1] + sy, vi[2] + sz, lane, K);
+    T sx = dx * step, sy = dy * step, sz = dz * step, su = du * step;
+    int kk = nn_query<T, NL::pow>(C, W, vi[0] + sx, vi[1] + sy, vi[2] + sz, lane, K, hi + su);
     K.lam++;
-    if (kk != i) { gx = sx; gy = sy; gz = sz; j = kk; break; }
+    if (kk != i) { gx = sx; gy = sy; gz = sz; gu = su; j = kk; break; }
   }
 search:
   for (int s = 0; s < C.max_search; ++s) {
     T wx = C.sites[3 * j] - vi[0], wy = C.sites[3 * j + 1] - vi[1], wz = C.sites[3 * j + 2] - vi[2];
-    T den = wx * gx + wy * gy + wz * gz;
+    T wu = NL::pow ? (T)C.lift[j] - hi : T(0);
+    T den = wx * gx + wy * gy + wz * gz + wu * gu;
     if (!(den > T(0))) { K.fallback++; return wit; }
-    T tt = T(0.5) * (wx * wx + wy * wy + wz * wz) / den;
+    T tt = T(0.5) * (wx * wx + wy * wy + wz * wz + wu * wu) / den;
     if (!(tt < T(1))) return j;
-    T sx = gx * tt, sy = gy * tt, sz = gz * tt;
-    int kk = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K);
+    T sx = gx * tt, sy = gy * tt, sz = gz * tt, su = gu * tt;
+    int kk = nn_search(C, W, L, i, vi, sx, sy, sz, lane, K, hi + su);
     K.search++;
     if (kk == i || kk == j) return j;
     j = kk;
-    gx = sx; gy = sy; gz = sz;
+    gx = sx; gy = sy; gz = sz; gu = su;
   }
   K.fallback++;
   return wit;
@@ -314,7 +326,7 @@ search:
 // clip the ring by plane pl, removing the outside run that contains corner p.
 // returns 0 clipped, 1 empty, -1 error.  nv is updated.
 template <typename T>
-__device__ __noinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int pl, int p, int& nv, int lane) {
+__device__ __forceinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int pl, int p, int& nv, int lane) {
   // a corner already proven inside Omega_i stays (inside every bisector half-space of v_i)
   bool o = lane < nv && W.vst[lane] != 1 && side_of(C, W, a, i, lane, nv, pl) < 0;
   unsigned om = __ballot_sync(FULL, o);
@@ -353,13 +365,22 @@ __device__ __noinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, int
   return 0;
 }
 
-template <typename T, bool EXT>
+template <typename T, bool EXT, bool POW = false>
 __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long long slot, int lane) {
   using V4 = typename Prec<T>::V4;
   Counters K = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T vi[3] = {C.sites[3 * i], C.sites[3 * i + 1], C.sites[3 * i + 2]};
-  const NbrList<T, EXT> L = load_nbrs<T, EXT>(C, i, lane);
+  const NbrList<T, EXT, POW> L = load_nbrs<T, EXT, POW>(C, i, lane);
+  // power diagram: B_ij in the lifted space meets u = 0 in the power bisector (Sec. 6.3)
+  auto lifted = [&](int j, V4& P, T& mx, T& mc) {
+    if (POW) {
+      T hj = (T)C.lift[j];
+      P.w += T(0.5) * (hj * hj - L.hi * L.hi);
+      mc += T(0.5) * (hj * hj + L.hi * L.hi);
+    }
+  };
   int np = 4, nv = 3;
+  if (lane == 0) W.tied = 0;
   if (lane < 4) {
     V4 P;
     T mx, mc;
@@ -413,12 +434,14 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       V4 P;
       T mx, mc;
       plane_B(C, j, vi, P, mx, mc);
+      lifted(j, P, mx, mc);
       if (lane == 0) { W.pn[pl] = P; W.pmx[pl] = mx; W.pmc[pl] = mc; W.psrc[pl] = j; }
       __syncwarp();
       if (side_of(C, W, a, i, p, nv, pl) >= 0) {
         K.fallback++;
         j = W.vwit[p];
         plane_B(C, j, vi, P, mx, mc);
+        lifted(j, P, mx, mc);
         __syncwarp();
         if (lane == 0) { W.pn[pl] = P; W.pmx[pl] = mx; W.pmc[pl] = mc; W.psrc[pl] = j; }
         __syncwarp();
@@ -481,13 +504,22 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
     mz = warp_sum(mz) + area * O.z;
     nonempty = area > T(0);
   }
+  // positive measure from the exact structure when no tie was met (as in 3D):
+  // a polygon of at least three corners and each of its edges
+  __syncwarp();
+  const bool exact_faces = W.tied == 0;
+  if (!empty && !nonempty && exact_faces) {
+    nonempty = true;
+    area = sizeof(T) == 4 ? T(1.17549435e-38) : T(2.2250738585072014e-308);
+    mx = my = mz = T(0);
+  }
   // edges of positive length: flags and propagation
   bool has = false, bis = false;
   int flag = 0;
   if (nonempty && lane < nv) {
     V4 A = W.vq[lane], B = W.vq[(lane + 1) % nv];
     T lx = B.x - A.x, ly = B.y - A.y, lz = B.z - A.z;
-    if (lx * lx + ly * ly + lz * lz > T(0)) {
+    if (exact_faces || lx * lx + ly * ly + lz * lz > T(0)) {
       int src = W.psrc[W.ve[lane]];
       bis = src >= 0;
       if (src >= 0) {

@@ -29,6 +29,10 @@ struct Dev {
   const unsigned* cmask; // [n] learned form: which of the 32 nearest are ranked candidates
   const int* knn2;       // [n*32] the 33rd..64th nearest (any order, -1 unused), or null
   const float* knn_r64;  // [n] certified radius of the 64 nearest (0: not certified)
+  // power diagrams (Sec. 6.3): site i lifted to (v_i, h_i), h_i = sqrt(eta - w_i);
+  // distances are taken to the lifted sites (null: Voronoi diagram)
+  const float* lift;     // [n] h_i
+  float lift_max;        // max_i h_i
   // pair set and queue
   unsigned long long* hash;
   unsigned long long hmask;
@@ -158,19 +162,27 @@ __device__ __forceinline__ void stat_add(const Dev<T>& C, int slot, unsigned lon
 // ---------------------------------------------------------------------------
 // EXT: the clip kernel is compiled with the 64-site tests (a separate
 // instantiation, so that workloads that do not need them keep the lean code).
-template <typename T, bool EXT = false>
+// POW: power diagram -- distances to the lifted sites (x, u) -> (v_k, h_k) with
+// the domain at u = 0; the lists are not used (the plain search only).
+template <typename T, bool EXT = false, bool POW = false>
 struct NbrList {
   static constexpr bool ext = EXT;
+  static constexpr bool pow = POW;
   int id;       // this lane's site (-1: none)
   T x, y, z;
   bool cand;
   float r32, r64;
+  T hi;         // power diagram: the lift h_i of the pair's site (0 otherwise)
 };
 
-template <typename T, bool EXT = false>
-__device__ __forceinline__ NbrList<T, EXT> load_nbrs(const Dev<T>& C, int i, int lane) {
-  NbrList<T, EXT> L;
-  L.id = -1; L.x = L.y = L.z = T(0); L.cand = false; L.r32 = 0.f; L.r64 = 0.f;
+template <typename T, bool EXT = false, bool POW = false>
+__device__ __forceinline__ NbrList<T, EXT, POW> load_nbrs(const Dev<T>& C, int i, int lane) {
+  NbrList<T, EXT, POW> L;
+  L.id = -1; L.x = L.y = L.z = T(0); L.cand = false; L.r32 = 0.f; L.r64 = 0.f; L.hi = T(0);
+  if (POW) {
+    L.hi = (T)C.lift[i];
+    return L;
+  }
   if (C.knn) {
     L.id = C.knn[(long long)i * 32 + lane];
     float d32 = C.knn_d2[(long long)i * 32 + 31];
@@ -217,11 +229,16 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
     T dx = vix - gx, dy = viy - gy, dz = viz - gz;
     di2 = dx * dx + dy * dy + dz * dz;
   }
+  // power diagram: the corner (q, 0) against the lifted site (v_i, h_i); every
+  // site closer to it in 4D is closer in 3D too, so the 3D scan radius below
+  // (from the 4D distance) covers them
+  if (NL::pow) di2 += L.hi * L.hi;
   T di = sqrt(di2);
   T gmax = fmax(fabs(gx), fmax(fabs(gy), fabs(gz)));
   T delta = T(1.7320508075688772) * (e + T(2) * U * gmax);
   T D = T(1.2) * di + delta;
   T B = T(4.5) * D * delta + T(2.5) * delta * delta + T(16) * U * D * D;
+  if (NL::pow) B += T(8) * U * (L.hi * L.hi + (T)C.lift_max * (T)C.lift_max);
   bool well = delta <= T(0.03) * di;
   T R = di * (T(1) + T(1e-5)) + T(2) * delta + T(4) * U * gmax;
   // ill-conditioned corner: every site that could be closer goes to the exact test
@@ -236,6 +253,10 @@ __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx,
     if (k == i || k == e0 || k == e1 || k == e2) return;
     T dx = s.x - gx, dy = s.y - gy, dz = s.z - gz;
     T d2 = dx * dx + dy * dy + dz * dz;
+    if (NL::pow) {
+      T hk = (T)C.lift[k];
+      d2 += hk * hk;
+    }
     T f = d2 - di2;
     if (d2 < bd || (d2 == bd && k < bk)) { bd = d2; bk = k; }
     if (f >= -B && f <= amb && (d2 < od || (d2 == od && k < ok)) && exact(k) < 0) { od = d2; ok = k; }

@@ -18,6 +18,13 @@ with the shapes the paper's experiments use, Sec. 6):
   * ``torus``    torus surface (R=1, r=0.3, 500,000 triangles), 200,000 sites
                  sampled by area and jittered off the surface
   * ``cube2m``   unit cube (6 tets), 2,000,000 uniform sites
+  * ``box``, ``box5m``  the unit cube as one box: 100,000 / 5,000,000 uniform
+                 sites (white noise)
+  * ``grid5m``   the unit cube as one box: 171^3 perturbed lattice centres
+  * ``blue5m``   box5m's sites marked for 100 Lloyd iterations of the library
+                 (blue noise by centroidal Voronoi relaxation, the paper's recipe)
+  * ``blue100k`` the unit cube as one box: 100,000 Poisson-disk (blue noise)
+                 sites drawn here, on the CPU
 """
 from __future__ import annotations
 
@@ -240,6 +247,52 @@ def perturbed_grid_sites(k: int, seed: int, amp: float = 0.1):
     return g.astype(np.float32).astype(np.float64)
 
 
+def poisson_disk_sites(n: int, seed: int, rounds: int = 6):
+    """Blue noise in the unit cube: dart throwing with a minimum distance r between
+    sites (Poisson-disk sampling), then n of the accepted sites kept at random.
+
+    Cells of edge r / sqrt(3) hold at most one site.  Cells are visited in 27
+    phases (cell index mod 3 per axis); within a phase no two cells are closer
+    than 2 r / sqrt(3) > r, so each empty cell draws one candidate and keeps it
+    if no site within r of it exists (cells within two of its own).  r is set
+    from the density such samples reach (about 0.65 / r^3 sites per unit
+    volume) so that the accepted sites exceed n.  Rounded to float32.
+    """
+    rng = _rng(seed)
+    r = (0.60 / n) ** (1.0 / 3.0)
+    G = int(np.ceil(np.sqrt(3.0) / r))
+    h = 1.0 / G
+    cell = -np.ones((G + 4,) * 3, dtype=np.int64)   # padded by 2: site index per cell
+    pts = np.zeros((0, 3))
+    grid = np.stack(np.meshgrid(np.arange(G), np.arange(G), np.arange(G), indexing="ij"), -1).reshape(-1, 3)
+    phases = [grid[np.all(grid % 3 == np.array(ph), axis=1)] for ph in itertools.product(range(3), repeat=3)]
+    offs = np.array([o for o in itertools.product(range(-2, 3), repeat=3) if o != (0, 0, 0)])
+    r2 = r * r
+    for _ in range(rounds):
+        for cells in phases:
+            cells = cells[cell[cells[:, 0] + 2, cells[:, 1] + 2, cells[:, 2] + 2] < 0]
+            if len(cells) == 0:
+                continue
+            cand = (cells + rng.uniform(0, 1, size=cells.shape)) * h
+            ok = np.ones(len(cells), dtype=bool)
+            for o in offs:
+                nb = cell[cells[:, 0] + 2 + o[0], cells[:, 1] + 2 + o[1], cells[:, 2] + 2 + o[2]]
+                has = nb >= 0
+                if not has.any():
+                    continue
+                d = pts[nb[has]] - cand[has]
+                bad = np.einsum("ij,ij->i", d, d) < r2
+                ok[np.nonzero(has)[0][bad]] = False
+            keep = np.nonzero(ok)[0]
+            cell[cells[keep, 0] + 2, cells[keep, 1] + 2, cells[keep, 2] + 2] = len(pts) + np.arange(len(keep))
+            pts = np.concatenate([pts, cand[keep]])
+    if len(pts) < n:
+        raise ValueError(f"Poisson-disk sampling kept {len(pts)} < {n} sites")
+    pts = pts[np.sort(rng.choice(len(pts), n, replace=False))]
+    out = np.clip(pts, 0.0, 1.0).astype(np.float32).astype(np.float64)
+    return _dedupe(out, lambda k: rng.uniform(0, 1, size=(k, 3)).astype(np.float32).astype(np.float64))
+
+
 def lattice_sites(N: int, dim: int, lo: float = 0.0, hi: float = 1.0):
     """Sites at the centres of an N^dim lattice of boxes: lo + (k+1/2) h."""
     h = (hi - lo) / N
@@ -344,6 +397,20 @@ def workload(name: str, n: int | None = None, seed: int | None = None):
         seed = (SEED_BASE + {"box": 2, "box5m": 7}[name]) if seed is None else seed
         sites = uniform_sites(n, 3, seed)
         return dict(name=name, mode=MODE_3D, sites=sites, verts=verts, simp=simp, f64=False,
+                    box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)))
+    if name == "blue5m":
+        # blue noise as the paper makes it (Sec. 6: sites relaxed by centroidal
+        # Voronoi tessellation): the 5M white-noise box sites, to be relaxed by
+        # `lloyd` graph-captured Lloyd iterations of the library before timing
+        w = workload("box5m", n, seed)
+        return dict(w, name=name, lloyd=100)
+    if name == "blue100k":
+        # blue noise drawn on the CPU (Poisson-disk dart throwing, no Voronoi
+        # arithmetic), for checks against the oracle
+        verts, simp = cube_6tet()
+        n = 100_000 if n is None else n
+        seed = SEED_BASE + 9 if seed is None else seed
+        return dict(name=name, mode=MODE_3D, sites=poisson_disk_sites(n, seed), verts=verts, simp=simp, f64=False,
                     box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)))
     if name == "grid5m":
         # perturbed grid: the centres of a 171^3 lattice (5,000,211 sites) moved by

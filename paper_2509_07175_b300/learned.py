@@ -21,6 +21,11 @@ INIT_SEED = 0x5EED
 # training recipe: 8 instances x 100,000 uniform sites in the unit cube (800,000
 # rows), 30 epochs of Adam, batch 1024, learning rate 1e-3
 N_INSTANCES, N_SITES, EPOCHS, BATCH, LR = 8, 100_000, 30, 1024, 1e-3
+# the headline's distribution beside the uniform cube: 4 cube and 4 clustered
+# shell instances (16 Gaussians, sigma 0.02, + 10 % uniform; 100,000 sites each,
+# so the clusters are sparser than at 1M -- the network's inputs are offsets
+# scaled by the nearest distance, which removes the density)
+MIX = (("cube", 4), ("shell", 4))
 
 
 def instance(n_sites: int, seed: int, name: str = "cube"):
@@ -36,12 +41,18 @@ def data_of(w: dict, options: dict | None = None):
     return x, y
 
 
-def training_set(n_instances: int = N_INSTANCES, n_sites: int = N_SITES, name: str = "cube"):
+def training_set(n_instances: int = N_INSTANCES, n_sites: int = N_SITES, name: str = "cube", mix=None):
+    """Features and labels of seeded instances: n_instances of `name`, or the
+    (name, count) pairs of `mix` (instance s of the whole set: seed TRAIN_SEED0 + s)."""
+    plan = list(mix) if mix else [(name, n_instances)]
     xs, ys = [], []
-    for s in range(n_instances):
-        x, y = data_of(instance(n_sites, TRAIN_SEED0 + s, name))
-        xs.append(x)
-        ys.append(y)
+    s = 0
+    for nm, count in plan:
+        for _ in range(count):
+            x, y = data_of(instance(n_sites, TRAIN_SEED0 + s, nm))
+            xs.append(x)
+            ys.append(y)
+            s += 1
     return torch.cat(xs), torch.cat(ys)
 
 
@@ -64,10 +75,11 @@ def train(x, y, epochs: int = EPOCHS, batch: int = BATCH, lr: float = LR, seed: 
             "epochs": epochs, "batch": batch, "lr": lr}
 
 
-def trained_state():
-    """Train the network with the default recipe; returns the training record."""
+def trained_state(mix=None):
+    """Train the network with the default recipe (or on the instances of `mix`);
+    returns the training record."""
     t0 = time.perf_counter()
-    x, y = training_set()
+    x, y = training_set(mix=mix)
     torch.cuda.synchronize()
     data_s = time.perf_counter() - t0
     tr = train(x, y)

@@ -50,6 +50,8 @@ def _load():
         lib.sv_destroy.restype = None
         lib.sv_run.restype = ctypes.POINTER(_Result)
         lib.sv_run.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+        lib.sv_run_list.restype = ctypes.POINTER(_Result)
+        lib.sv_run_list.argtypes = [P, P, ctypes.c_int64]
         lib.sv_free_result.argtypes = [ctypes.POINTER(_Result)]
         lib.sv_free_result.restype = None
         _lib = lib
@@ -104,6 +106,15 @@ class Serial:
         """Alg. 2 over simplices [a0, a1)."""
         a1 = len(self.simp) if a1 is None else a1
         r = _load().sv_run(self._h, int(a0), int(a1))
+        try:
+            return Pieces(r.contents)
+        finally:
+            _load().sv_free_result(r)
+
+    def run_list(self, simplices):
+        """Alg. 2 over the listed simplices (a sample of the mesh)."""
+        lst = np.ascontiguousarray(simplices, dtype=np.int64)
+        r = _load().sv_run_list(self._h, lst.ctypes.data_as(ctypes.c_void_p), len(lst))
         try:
             return Pieces(r.contents)
         finally:

@@ -255,6 +255,20 @@ static inline void cell_range(const Grid* G, const double* p, double r, int lo[3
     }                                                                                         \
   })
 
+/* cell size where p lies: the finer grid's inside a dense cell */
+static double local_h(const sv_ctx* c, const double* p) {
+  const Grid* G = &c->g;
+  double o[3] = {G->ox, G->oy, G->oz};
+  int gd[3] = {G->gx, G->gy, G->gz}, id[3];
+  for (int d = 0; d < 3; ++d) {
+    double a = (p[d] - o[d]) / G->h;
+    long long x = (long long)floor(a < -1e9 ? -1e9 : (a > 1e9 ? 1e9 : a));
+    id[d] = (int)(x < 0 ? 0 : (x >= gd[d] ? gd[d] - 1 : x));
+  }
+  long long q = ((long long)id[2] * G->gy + id[1]) * G->gx + id[0];
+  return G->sub[q] >= 0 ? c->fine[G->sub[q]].h : G->h;
+}
+
 /* nearest site of p (ties: smaller index), skipping `skip` and the sites ex0,
  * ex1; grows the ball from the local cell size until it holds a site, then
  * rescans the ball of the best distance */
@@ -269,7 +283,7 @@ static int nearest_ex(sv_ctx* c, const double* p, int skip, int ex0, int ex1, do
     double dd = dx * dx + dy * dy + dz * dz;                                \
     if (dd < bd || (dd == bd && k < bi)) { bd = dd; bi = k; }               \
   }
-  double r = c->g.h;
+  double r = local_h(c, p);
   for (int it = 0; it < 64 && bi < 0; ++it, r *= 2) FOR_BALL(c, p, r, k, NN_BODY);
   if (bi < 0) { *d2 = 1e300; return -1; }
   double rb = sqrt(bd) * (1 + 1e-12) + 1e-300;
@@ -597,7 +611,7 @@ static int corner_test(sv_ctx* c, const Poly* P, const Corner* q, int s, int* wi
     F = da_ - ds2;                                                                         \
     BOUND = 2.0 * 1.7320508075688772 * err * (sqrt(da_) + rs) + 3 * err * err + 8 * U64 * (da_ + ds2) + 1e-300; \
   }
-  if (rs > 2 * c->g.h) {  /* far from its site (a simplex corner): the nearest site decides first */
+  if (rs > 2 * local_h(c, qg)) {  /* far from its site (a simplex corner): the nearest site decides first */
     double d2;
     int k = nearest_ex(c, qg, ex[2], ex[0], ex[1], &d2);
     if (k >= 0 && k != s) {
@@ -1095,9 +1109,16 @@ void sv_destroy(sv_ctx* c) {
   free(c);
 }
 
-/* Alg. 2 over the simplices [a0, a1): every piece (also empty ones are not
- * produced: a piece is emitted for each site reached), with counters */
-sv_result* sv_run(sv_ctx* c, int64_t a0, int64_t a1) {
+static sv_result* run_simplices(sv_ctx* c, int64_t a0, int64_t a1, const int64_t* list, int64_t nlist);
+
+/* Alg. 2 over the simplices [a0, a1): a piece for each site reached (empty ones
+ * included, with measure 0), with counters */
+sv_result* sv_run(sv_ctx* c, int64_t a0, int64_t a1) { return run_simplices(c, a0, a1, NULL, 0); }
+
+/* the same over a list of simplex indices (a sample of the mesh) */
+sv_result* sv_run_list(sv_ctx* c, const int64_t* list, int64_t nlist) { return run_simplices(c, 0, 0, list, nlist); }
+
+static sv_result* run_simplices(sv_ctx* c, int64_t a0, int64_t a1, const int64_t* list, int64_t nlist) {
   sv_result* R = (sv_result*)calloc(1, sizeof(sv_result));
   Poly* buf = (Poly*)malloc(2 * sizeof(Poly));
   JobQ Q = {NULL, 0, 0, 0};
@@ -1105,11 +1126,17 @@ sv_result* sv_run(sv_ctx* c, int64_t a0, int64_t a1) {
   memset(&O, 0, sizeof(O));
   if (!R || !buf) { free(R); free(buf); return NULL; }
   memset(c->stats, 0, sizeof(c->stats));
+  for (int64_t i = 0; i < c->n; ++i) c->stamp[i] = -1;  /* visit marks are per simplex and per run */
   if (a0 < 0) a0 = 0;
   if (a1 > c->m) a1 = c->m;
+  if (a1 < a0) a1 = a0;
   int status = 0;
-  for (int64_t a = a0; a < a1; ++a)
+  int64_t cnt = list ? nlist : a1 - a0;
+  for (int64_t t = 0; t < cnt; ++t) {
+    int64_t a = list ? list[t] : a0 + t;
+    if (a < 0 || a >= c->m) { status = -1; continue; }
     if (simplex_pieces(c, (int)a, &O, buf, &Q)) { status = -1; c->stats[S_ERROR]++; }
+  }
   if (out_reserve(&O, O.np + 1, O.nf + 1)) status = -2;
   if (!O.foff) { O.foff = (int64_t*)calloc(1, sizeof(int64_t)); }
   R->np = O.np;

@@ -13,7 +13,7 @@ import torch
 import oracle as O
 from paper_2509_07175_b300 import binding as B
 from paper_2509_07175_b300 import inputs as I
-from vdcheck import compare_full
+from vdcheck import compare_full, compare_population
 
 pytestmark = pytest.mark.gpu
 
@@ -59,11 +59,10 @@ def test_graph_equals_eager(gpu, name, n, iters):
 def test_cube_10_iterations_graph_per_iteration_parity(gpu):
     """Config 2: 100,000 uniform sites in the 6-tet cube, 10 Lloyd iterations
     replayed from one captured graph; at every iteration the diagram of that
-    iteration's sites matches the oracle on a sample of 150 sites, the update
-    moves each site exactly to its centroid, and the mean displacement shrinks."""
+    iteration's sites matches the oracle on every site, the update moves each
+    site exactly to its centroid, and the mean displacement shrinks."""
     w = I.workload("cube")
     d = _diag(w)
-    rng = np.random.default_rng(21)
     moves = []
     for it in range(10):
         s_before = _sites_np(d, w)
@@ -76,10 +75,8 @@ def test_cube_10_iterations_graph_per_iteration_parity(gpu):
         assert np.array_equal(s_after, c)   # v_i <- centroid_i, bit for bit
         moves.append(float(np.linalg.norm(s_after - s_before, axis=1).mean()))
         wk = dict(w, sites=s_before)
-        pick = np.sort(rng.choice(len(s_before), 150, replace=False))
-        op = O.Oracle(4, s_before, w["verts"], w["simp"]).site_pieces(pick)
-        p = d.pieces()
-        compare_full(wk, r, p, op, sites_subset=pick)
+        op = O.Oracle(4, s_before, w["verts"], w["simp"]).all_sites()
+        compare_population(wk, r, d.pieces(), op)
     assert all(moves[k + 1] < moves[k] for k in range(len(moves) - 1)), moves
     d.close()
 
@@ -87,7 +84,7 @@ def test_cube_10_iterations_graph_per_iteration_parity(gpu):
 def test_torus_50_iterations_graph(gpu):
     """Config 4: restricted diagram on the 500,000-triangle torus, 200,000
     sites, 50 graph-captured Lloyd iterations; the 50th iteration's diagram
-    matches the oracle on a sample of sites and partitions the surface."""
+    matches the oracle on every site and partitions the surface."""
     w = I.workload("torus")
     d = _diag(w, stats=1)
     d.lloyd(49, use_graph=True)
@@ -98,10 +95,8 @@ def test_torus_50_iterations_graph(gpu):
     pm = p["measure"].double().cpu().numpy()
     total = I.domain_measure(w["mode"], w["verts"], w["simp"])
     assert abs(pm.sum() - total) < 1e-5 * total
-    rng = np.random.default_rng(23)
-    pick = np.sort(rng.choice(len(s49), 150, replace=False))
-    op = O.Oracle(w["mode"], s49, w["verts"], w["simp"]).site_pieces(pick)
-    compare_full(dict(w, sites=s49), r, p, op, sites_subset=pick)
+    op = O.Oracle(w["mode"], s49, w["verts"], w["simp"]).all_sites()
+    compare_population(dict(w, sites=s49), r, p, op)
     d.close()
 
 

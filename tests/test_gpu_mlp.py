@@ -228,3 +228,31 @@ def test_trained_network_gain(gpu):
     assert q["net16"][0] < q["plain"][0]
     assert q["net16"][1] > q["dist16"][1]
     d.close()
+
+
+def test_network_on_the_shell_distribution(gpu):
+    """The bench's recipe: trained on 4 cube and 4 clustered-shell instances,
+    evaluated on a held-out shell instance.  Reports the recall of neighbours
+    among the top k against the distance ranking and the untrained network; the
+    trained ranking must beat the untrained one clearly and not fall behind the
+    distance ranking, and the learned form stays bit-identical to the plain one."""
+    tr = L.trained_state(mix=L.MIX)
+    w = L.instance(100_000, L.HELDOUT_SEED, "shell")
+    xv, yv = L.data_of(w)
+    z_trained = L.logits_of(tr["state"], xv)
+    z_random = L.logits_of(L.random_init_state(), xv)
+    z_dist = -torch.arange(32, device="cuda", dtype=torch.float32).expand(xv.shape[0], 32)
+    rec = {k: (L.recall_at_k(z_trained, yv, k), L.recall_at_k(z_dist, yv, k), L.recall_at_k(z_random, yv, k))
+           for k in (4, 8, 16, 24)}
+    print("shell recall@k (trained, distance, untrained):", rec)
+    for k in (8, 16):
+        assert rec[k][0] > rec[k][2] + 0.1, k
+        assert rec[k][0] > rec[k][1] - 0.01, k
+    d = B.diagram_from_workload(w)
+    plain = d.compute()
+    L.load_state(d, tr["state"])
+    d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=24, split=1)
+    lr = d.compute()
+    for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+        assert torch.equal(plain[key], lr[key]), key
+    d.close()

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Bar (the benchmark spec): bit-exact neighbour sets and clip topology (the set of
+Bar: bit-exact neighbour sets and clip topology (the set of
 non-empty (simplex, site) pieces and each piece's face flags); per-site
 measures within 1e-5 relative; centroids within 1e-5 |c|.  Inputs are the
 seeded generators of ``paper_2509_07175_b300.inputs``.
@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 from paper_2509_07175_b300 import inputs as I
-from vdcheck import compare_full, gpu_csr, gpu_run
+from vdcheck import compare_full, compare_population, gpu_csr, gpu_run
 
 pytestmark = pytest.mark.gpu
 
@@ -111,36 +111,46 @@ def test_deterministic_bitwise(gpu):
         assert torch.equal(r1[k], r2[k]), k
 
 
-def test_cube_100k_sampled(gpu):
-    """Config 2 at full size: 100,000 sites in the 6-tet cube; oracle on a sample
-    of sites (all their pieces), plus the partition of the domain."""
-    w = I.workload("cube")
-    d, r, p = gpu_run(w)
-    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
-    pm = p["measure"].double().cpu().numpy()
-    assert abs(pm.sum() - 1.0) < 1e-5
-    per = np.zeros(6)
-    np.add.at(per, p["simplex"].cpu().numpy(), pm)
-    np.testing.assert_allclose(per, 1.0 / 6.0, rtol=1e-5)
-    rng = np.random.default_rng(7)
-    pick = np.sort(rng.choice(len(w["sites"]), 300, replace=False))
-    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
-    compare_full(w, r, p, op, sites_subset=pick)
+KEYS = ("measure", "centroid", "nbr_off", "nbr_idx")
+BENCH_FORM = dict(learned=1, topk=24, split=1, mapping=0)  # the form bench.py times (autotuned mapping)
 
 
-def test_shell_1m_sampled(gpu):
-    """Config 3 at full size: 1,000,000 clustered sites in the tetrahedralised shell
-    (172,032 tets); oracle on a sample of sites, plus the partition of the shell."""
-    w = I.workload("shell")
-    d, r, p = gpu_run(w)
-    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
-    pm = p["measure"].double().cpu().numpy()
-    total = I.domain_measure(4, w["verts"], w["simp"])
-    assert abs(pm.sum() - total) < 1e-5 * total
-    rng = np.random.default_rng(11)
-    pick = np.sort(rng.choice(len(w["sites"]), 200, replace=False))
-    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
-    compare_full(w, r, p, op, sites_subset=pick)
+def _population(name, forms):
+    """Whole-population parity of a full-size workload: the oracle on every site,
+    compared with each form's result; the forms must also agree bit for bit."""
+    w = I.workload(name)
+    op = O.Oracle(w["mode"], w["sites"], w["verts"], w["simp"]).all_sites()
+    assert op.stats["uncertain"] == 0
+    from paper_2509_07175_b300 import binding as B
+    d = B.diagram_from_workload(w)
+    errs, first = {}, None
+    for label, opts in forms:
+        d.set_options(**opts)
+        r = d.compute()
+        assert r["status"] == 0
+        p = d.pieces()
+        errs[label] = compare_population(w, r, p, op, split=bool(opts.get("split")))
+        if first is None:
+            first = r
+        else:
+            for k in KEYS:
+                assert torch.equal(first[k], r[k]), (label, k)
+    d.close()
+    print(name, errs)
+    return errs
+
+
+def test_cube_100k_full(gpu):
+    """Config 2 at full size, every site: 100,000 sites in the 6-tet cube, the plain
+    per-tetrahedron form and the learned + split form as timed."""
+    _population("cube", [("plain", dict()), ("bench", BENCH_FORM)])
+
+
+def test_shell_1m_full(gpu):
+    """Config 3 at full size, every site: 1,000,000 clustered sites in the
+    tetrahedralised shell (172,032 tets); the plain per-tetrahedron form and the
+    learned + split form as timed; bit-identical to each other."""
+    _population("shell", [("plain", dict()), ("bench", BENCH_FORM)])
 
 
 @pytest.mark.parametrize("name,n", [("cube", 20000), ("shell", 30000), ("square", 1000), ("torus", 20000)])
@@ -190,21 +200,19 @@ def test_coincident_sites_are_reported(gpu, mode):
     d.close()
 
 
-def test_cube2m_sampled(gpu):
-    """Config 5 at full size: 2,000,000 uniform sites in the 6-tet cube; oracle on
-    a sample of sites, learned form (network ranking) bit-identical to plain."""
+def test_cube2m_full(gpu):
+    """Config 5 at full size, every site: 2,000,000 uniform sites in the 6-tet cube
+    (learned + split as timed), and the learned form with a network ranking
+    (untrained) bit-identical to it."""
     from paper_2509_07175_b300 import binding as B
+    _population("cube2m", [("bench", BENCH_FORM)])
     w = I.workload("cube2m")
-    d, r, p = gpu_run(w)
-    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
-    rng = np.random.default_rng(41)
-    pick = np.sort(rng.choice(len(w["sites"]), 150, replace=False))
-    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
-    compare_full(w, r, p, op, sites_subset=pick)
+    d = B.diagram_from_workload(w, options=BENCH_FORM)
+    r = d.compute()
     d.mlp_init(9)
-    d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=24)
+    d.set_options(proposal=B.PROPOSAL_MLP, **BENCH_FORM)
     lr = d.compute()
-    for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
+    for key in KEYS:
         assert torch.equal(r[key], lr[key]), key
     d.close()
 

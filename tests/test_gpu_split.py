@@ -140,21 +140,3 @@ def test_split_lloyd_graph(gpu):
     b.close()
 
 
-def test_split_shell_1m_sampled(gpu):
-    """The 1M-site shell (172,032 tets) at full size in split mode, learned form
-    as timed: oracle on a sample of sites, the partition of the shell, and the
-    learned form bit-identical to the plain one."""
-    w = I.workload("shell")
-    d, r, p = gpu_run(w, options=dict(learned=1, topk=24, **SPLIT))
-    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
-    total = I.domain_measure(4, w["verts"], w["simp"])
-    assert abs(float(p["measure"].double().sum()) - total) < 1e-5 * total
-    rng = np.random.default_rng(71)
-    pick = np.sort(rng.choice(len(w["sites"]), 200, replace=False))
-    op = O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(pick)
-    compare_full(w, r, p, op, sites_subset=pick, split=True)
-    d.set_options(**SPLIT)
-    plain = d.compute()
-    for k in KEYS:
-        assert torch.equal(plain[k], r[k]), k
-    d.close()

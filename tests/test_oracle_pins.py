@@ -326,3 +326,69 @@ def test_power_planted_sign_flip_is_caught():
             assert abs(meas[0] - 0.4) > 1e-3
         finally:
             O._lib = saved
+
+
+# ----- power diagrams restricted to a surface (mode 3) -----------------------------
+
+def _surface_power_case(n, seed):
+    v, s = I.torus_domain(nu=36, nv=12)
+    sites = I.surface_sites(n, v, s, seed)
+    measure = I.domain_measure(3, v, s)
+    rng = np.random.default_rng(seed)
+    return v, s, sites, rng.uniform(-measure / n, measure / n, n)
+
+
+def test_power_surface_equal_weights_is_voronoi():
+    """Equal weights cancel in every power bisector, on a surface too."""
+    v, s, sites, _ = _surface_power_case(90, 41)
+    pv = O.Oracle(3, sites, v, s).enumerate()
+    pw = O.Oracle(3, sites, v, s, weights=np.full(len(sites), -0.21)).enumerate()
+    _compare(pv, pw, tol=1e-12)
+
+
+@pytest.mark.parametrize("n,seed", [(70, 42), (40, 43)])
+def test_power_surface_brute_equals_security_radius(n, seed):
+    """Restricted power diagram on a torus: all n-1 power bisectors against the
+    generalised security radius, and the cells partition the surface."""
+    v, s, sites, w = _surface_power_case(n, seed)
+    pb = O.Oracle(3, sites, v, s, brute=True, weights=w).enumerate()
+    ps = O.Oracle(3, sites, v, s, brute=False, weights=w).enumerate()
+    _compare(pb, ps)
+    total = I.domain_measure(3, v, s)
+    assert abs(pb.meas.sum() - total) < 1e-10 * total
+
+
+@pytest.mark.parametrize("e1,e2,dw", [(0.0, 0.0, 0.1), (0.1, 0.0, 0.0), (0.05, 0.2, -0.1), (0.3, 0.1, 0.2)])
+def test_power_surface_two_sites_off_the_plane(e1, e2, dw):
+    """A planar square mesh (z = 0) in surface mode, two sites at heights e1, e2
+    above it with weights 0 and dw: on the plane the power distance of site i is
+    (x - x_i)^2 + (y - 1/2)^2 + e_i^2 - w_i, so the cells meet on the line
+    x* = 1/2 - dw + e2^2 - e1^2 (sites at x = 1/4 and 3/4)."""
+    v, s = I.square_2tri()
+    sites = np.array([[0.25, 0.5, e1], [0.75, 0.5, e2]])
+    p = O.Oracle(3, sites, v, s, brute=True, weights=np.array([0.0, dw])).enumerate()
+    meas, cen, nb = O.per_site(2, sites, p)
+    xs = 0.5 - dw + e2 ** 2 - e1 ** 2
+    assert 0 < xs < 1
+    assert abs(meas[0] - xs) < 1e-12 and abs(meas[1] - (1 - xs)) < 1e-12
+    assert abs(cen[0][0] - xs / 2) < 1e-12 and abs(cen[1][0] - (1 + xs) / 2) < 1e-12
+    assert abs(cen[0][2]) < 1e-12 and abs(cen[1][2]) < 1e-12   # centroids lie on the surface
+    assert nb[0] == [1] and nb[1] == [0]
+
+
+@pytest.mark.parametrize("mode", [2, 3, 4])
+def test_all_sites_equals_enumeration(mode):
+    """The per-site form over every site (used for whole-population checks at full
+    size, parallel over sites) gives exactly the pieces of the per-simplex form."""
+    if mode == 2:
+        v, s = I.square_grid_tris(3)
+        sites = I.uniform_sites(400, 2, 95, f32=False)
+    elif mode == 3:
+        v, s = I.torus_domain(nu=30, nv=10)
+        sites = I.surface_sites(300, v, s, 96)
+    else:
+        v, s = I.kuhn_lattice_tets(2)
+        sites = I.uniform_sites(500, 3, 97)
+    o = O.Oracle(mode, sites, v, s)
+    a, b = o.enumerate(), o.all_sites()
+    _compare(a, b, tol=0.0)
