@@ -687,7 +687,11 @@ static int clip_by_site(workspace* w, int64_t j) {
   return w->P.C->mode == ORC_MODE_3D ? poly_clip(&w->P, w->G3, idx) : pgon_clip(&w->P, w->G2, idx);
 }
 
-static void integrate(workspace* w, int64_t a, piece_out* o) {
+/* exact: no sign decision of this piece was a tie or left uncertain, so the
+   clipped piece is a simple polytope (polygon) whose every face (edge) has
+   positive measure, as has the piece itself -- whatever float64 makes of a
+   sliver far below its resolution.  Otherwise the computed measures decide. */
+static void integrate(workspace* w, int64_t a, piece_out* o, int exact) {
   const orc_ctx* C = w->P.C;
   o->meas = 0; o->m1[0] = o->m1[1] = o->m1[2] = 0; o->nf = 0;
   if (C->mode == ORC_MODE_3D) {
@@ -710,7 +714,7 @@ static void integrate(workspace* w, int64_t a, piece_out* o) {
         az += u[0] * v[1] - u[1] * v[0];
       }
       double area = 0.5 * sqrt(ax * ax + ay * ay + az * az);
-      if (area > 0) {
+      if (area > 0 || exact) {
         o->flags[o->nf] = w->P.pl[G->fpl[f]].flag;
         o->fmeas[o->nf] = area;
         o->nf++;
@@ -744,12 +748,18 @@ static void integrate(workspace* w, int64_t a, piece_out* o) {
       const double* r = G->v[(k + 1) % G->n].q;
       double len = sqrt((r[0] - p[0]) * (r[0] - p[0]) + (r[1] - p[1]) * (r[1] - p[1]) +
                         (r[2] - p[2]) * (r[2] - p[2]));
-      if (len > 0) {
+      if (len > 0 || exact) {
         o->flags[o->nf] = w->P.pl[G->e[k]].flag;
         o->fmeas[o->nf] = len;
         o->nf++;
       }
     }
+  }
+  if (exact && !(o->meas > 0)) {
+    /* positive in exact arithmetic, below float64 resolution: the smallest
+       normal double as its measure, no moment */
+    o->meas = 2.2250738585072014e-308;
+    o->m1[0] = o->m1[1] = o->m1[2] = 0;
   }
 }
 
@@ -757,6 +767,7 @@ static void compute_piece(workspace* w, int64_t a, int64_t i, piece_out* o) {
   const orc_ctx* C = w->P.C;
   init_piece(w, a, i);
   w->P.st[ST_PIECES]++;
+  const int64_t undecided0 = w->P.st[ST_TIE] + w->P.st[ST_UNCERTAIN];
   int rc = 0;
   if (C->brute) {
     for (int64_t j = 0; j < C->n && rc == 0; ++j) {
@@ -794,7 +805,7 @@ static void compute_piece(workspace* w, int64_t a, int64_t i, piece_out* o) {
   }
   o->status = rc < 0 ? -1 : 0;
   if (rc < 0 || piece_empty(w)) { o->meas = 0; o->m1[0] = o->m1[1] = o->m1[2] = 0; o->nf = 0; return; }
-  integrate(w, a, o);
+  integrate(w, a, o, w->P.st[ST_TIE] + w->P.st[ST_UNCERTAIN] == undecided0);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -214,7 +214,7 @@ __device__ __noinline__ float4 refine64(const Dev<float>& C, int a, int i, int s
 }
 
 // ----- exact side tests ----------------------------------------------------------
-__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4, bool mark = false) {
+__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4, int* unsure = nullptr) {
   ePlane p[4];
   uchar4 v = W.tv[t];
   // the corner lies on each of its own planes: the side value is exactly zero
@@ -227,7 +227,7 @@ __device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int 
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
-    if (mark) W.tied = 1;  // a clip decision met a tie: positivity from the measures
+    if (unsure) *unsure = 1;  // positivity then follows the measures (see process_pair)
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, W.psrc[v.x], W.psrc[v.y], W.psrc[v.z], src4, tie, 0);
   }
@@ -246,7 +246,7 @@ __device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int 
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return exact_side(C, W, a, i, t, W.psrc[pl], true);
+  return exact_side(C, W, a, i, t, W.psrc[pl], &W.tied);
 }
 
 // ----- one pair ------------------------------------------------------------------
@@ -875,10 +875,14 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       int ex[3];
       ex[0] = W.psrc[v.x]; ex[1] = W.psrc[v.y]; ex[2] = W.psrc[v.z];
       for (int u = 0; u < 3; ++u) if (ex[u] < 0) ex[u] = -2;  // tet faces exclude no site
-      auto exact = [&](int k) { return exact_side(C, W, a, i, t, k); };
+      int uns = 0;
+      auto exact = [&](int k) { return exact_side(C, W, a, i, t, k, &uns); };
       int wit;
       int sc = 0, ls = 0;
       int out = corner_outside(C, i, vi.x, vi.y, vi.z, q.x, q.y, q.z, q.w, ex, lane, W.S, L, exact, &wit, &sc, &ls);
+      // a corner found inside with a tie (or an uncertain sign) lies on that
+      // site's bisector: the polytope may be degenerate there
+      if (__any_sync(FULL, uns) && !out && lane == 0) W.tied = 1;
       K.corner++;
       K.nn++;
       K.scanned += sc;

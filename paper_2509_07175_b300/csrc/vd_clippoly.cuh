@@ -155,7 +155,7 @@ __device__ __noinline__ typename Prec<T>::V4 refine(const Dev<T>& C, const WarpP
 }
 
 template <typename T>
-__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4, bool mark = false) {
+__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4, int* unsure = nullptr) {
   int km = (k + nv - 1) % nv;
   // the corner lies on each of its own planes: the side value is exactly zero
   if (src4 == -1 || src4 == W.psrc[W.ve[km]] || src4 == W.psrc[W.ve[k]]) return 0;
@@ -168,7 +168,7 @@ __device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
-    if (mark) W.tied = 1;  // a clip decision met a tie: positivity from the measures
+    if (unsure) *unsure = 1;  // positivity then follows the measures (see process_pair)
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, -1, W.psrc[W.ve[km]], W.psrc[W.ve[k]], src4, tie, 0);
   }
@@ -185,7 +185,7 @@ __device__ __forceinline__ int side_of(const Dev<T>& C, const WarpP<T>& W, int a
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return exact_side(C, W, a, i, k, nv, W.psrc[pl], true);
+  return exact_side(C, W, a, i, k, nv, W.psrc[pl], &W.tied);
 }
 
 struct Counters {
@@ -412,9 +412,13 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       if (ex[0] < 0) ex[0] = -2;
       if (ex[1] < 0) ex[1] = -2;
       int nvv = nv, kk = k;
-      auto exact = [&](int site) { return exact_side(C, W, a, i, kk, nvv, site); };
+      int uns = 0;
+      auto exact = [&](int site) { return exact_side(C, W, a, i, kk, nvv, site, &uns); };
       int wit, sc = 0, ls = 0;
       int out = corner_outside(C, i, vi[0], vi[1], vi[2], q.x, q.y, q.z, q.w, ex, lane, W.S, L, exact, &wit, &sc, &ls);
+      // a corner found inside with a tie (or an uncertain sign) lies on that
+      // site's bisector: the polygon may be degenerate there
+      if (__any_sync(FULL, uns) && !out && lane == 0) W.tied = 1;
       K.corner++;
       K.nn++;
       K.scanned += sc;

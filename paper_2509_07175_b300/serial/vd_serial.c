@@ -803,8 +803,12 @@ static int face_cycle(const Poly* P, int x, int* cyc) {
 }
 
 /* measure of the face on every plane slot (area in 3D, length of a polygon's
- * edge; 0 when the plane bounds no face of positive measure) */
-static void face_measures(const sv_ctx* c, const Poly* P, double* fm) {
+ * edge; 0 when the plane bounds no face of positive measure).  exact: no sign
+ * decision of the piece was a tie or uncertain, so the piece is a simple
+ * polytope (polygon) and every plane holding a face cycle bounds a face of
+ * positive measure, however small its float64 value (the smallest normal
+ * double stands in for one that rounds to zero). */
+static void face_measures(const sv_ctx* c, const Poly* P, double* fm, int exact) {
   int cyc[MAXV];
   int polygon = c->k == 3;
   for (int x = 0; x < P->npl; ++x) {
@@ -833,6 +837,7 @@ static void face_measures(const sv_ctx* c, const Poly* P, double* fm) {
       }
       fm[x] = 0.5 * sqrt(sum[0] * sum[0] + sum[1] * sum[1] + sum[2] * sum[2]);
     }
+    if (exact && !(fm[x] > 0) && n >= (polygon ? 2 : 3)) fm[x] = 2.2250738585072014e-308;
   }
 }
 
@@ -846,7 +851,8 @@ static int32_t flag_of(const sv_ctx* c, int a, int src) {
  * fan of tetrahedra around the corners' mean), first moment in the frame of
  * v_s, and the flags of its faces of positive measure.  clipped[x]: plane x was
  * added by a clip of Alg. 1 (for the count of clips that left no face). */
-static double piece_emit(sv_ctx* c, const Poly* P, int s, Out* O, const double* fm, const unsigned char* clipped) {
+static double piece_emit(sv_ctx* c, const Poly* P, int s, Out* O, const double* fm, const unsigned char* clipped,
+                         int exact) {
   int cyc[MAXV];
   double meas = 0, m1[3] = {0, 0, 0};
   int64_t p = O->np;
@@ -887,6 +893,11 @@ static double piece_emit(sv_ctx* c, const Poly* P, int s, Out* O, const double* 
           m1[d] += v * ((ref[d] + P->v[cyc[0]].x[d] + P->v[cyc[t]].x[d] + P->v[cyc[t + 1]].x[d]) / 4.0);
       }
     }
+  }
+  if (exact && !(meas > 0) && P->nc >= (c->k == 3 ? 3 : 4)) {
+    /* positive in exact arithmetic, below float64 resolution */
+    meas = 2.2250738585072014e-308;
+    m1[0] = m1[1] = m1[2] = 0;
   }
   int nclip = 0, contrib = 0;
   for (int x = 0; x < P->npl; ++x) nclip += clipped[x];
@@ -961,6 +972,7 @@ static int simplex_pieces(sv_ctx* c, int a, Out* O, Poly* buf, JobQ* Q) {
   unsigned char clipped[MAXPL];
   int i = nearest(c, c0, -1, &d2);
   if (i < 0) return -1;
+  int64_t und = c->stats[S_TIES] + c->stats[S_UNCERTAIN];  /* undecided signs before the piece */
   for (int guard = 0;; ++guard) {  /* the first corner lies in Omega_i (ties: inside) */
     int wit;
     poly_simplex(c, P, a, i);
@@ -973,14 +985,16 @@ static int simplex_pieces(sv_ctx* c, int a, Out* O, Poly* buf, JobQ* Q) {
   c->stamp[i] = a;
   memset(clipped, 0, sizeof(clipped));
   if (alg1(c, P, i, clipped) < 0) return -1;
-  face_measures(c, P, fm);
-  double m = piece_emit(c, P, i, O, fm, clipped);
+  int exact = c->stats[S_TIES] + c->stats[S_UNCERTAIN] == und;
+  face_measures(c, P, fm, exact);
+  double m = piece_emit(c, P, i, O, fm, clipped, exact);
   if (m < 0) return -1;
   if (m > 0 && queue_faces(c, P, fm, a, i, Q)) return -1;
   while (Q->head < Q->n) {
     Job J = Q->q[Q->head++];
     int j = J.j;
     /* G_{a,j}: T_a clipped by B_{j,u} and by B_{j,w} for the faces adjacent to f */
+    und = c->stats[S_TIES] + c->stats[S_UNCERTAIN];
     poly_simplex(c, G, a, j);
     int h = add_plane(c, G, J.u), r = 0, hu = h;
     if (h < 0) return -1;
@@ -1006,8 +1020,9 @@ static int simplex_pieces(sv_ctx* c, int a, Out* O, Poly* buf, JobQ* Q) {
     if (!started) { c->stats[S_ERROR]++; continue; }
     memset(clipped, 0, sizeof(clipped));
     if (alg1(c, G, j, clipped) < 0) return -1;
-    face_measures(c, G, fm);
-    m = piece_emit(c, G, j, O, fm, clipped);
+    exact = c->stats[S_TIES] + c->stats[S_UNCERTAIN] == und;
+    face_measures(c, G, fm, exact);
+    m = piece_emit(c, G, j, O, fm, clipped, exact);
     if (m < 0) return -1;
     if (m > 0 && queue_faces(c, G, fm, a, j, Q)) return -1;
   }

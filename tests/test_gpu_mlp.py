@@ -248,10 +248,10 @@ def test_network_on_the_shell_distribution(gpu):
     for k in (8, 16):
         assert rec[k][0] > rec[k][2] + 0.1, k
         assert rec[k][0] > rec[k][1] - 0.01, k
-    d = B.diagram_from_workload(w)
+    d = B.diagram_from_workload(w, options=dict(split=1, mapping=1))
     plain = d.compute()
     L.load_state(d, tr["state"])
-    d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=24, split=1)
+    d.set_options(learned=1, proposal=B.PROPOSAL_MLP, topk=24, split=1, mapping=1)
     lr = d.compute()
     for key in ("measure", "centroid", "nbr_off", "nbr_idx"):
         assert torch.equal(plain[key], lr[key]), key
