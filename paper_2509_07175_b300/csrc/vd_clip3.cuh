@@ -48,7 +48,6 @@ struct Warp3 {
   unsigned char prank[MAXP];      // rank of each face among the faces by source (integration)
   float4 contrib[MAXT]; // volume / moment terms by corner rank (integration)
   ScanScratch S;
-  CornerScratch A;
 };
 
 // warp-uniform bookkeeping (identical in every lane)

@@ -36,7 +36,6 @@ struct WarpP {
   int vwit[MAXV];
   mutable int tied;  // this pair met an exact tie or an uncertain sign
   ScanScratch S;
-  CornerScratch A;
 };
 
 template <typename T> __device__ __forceinline__ T gam() { return T(64) * Prec<T>::U; }

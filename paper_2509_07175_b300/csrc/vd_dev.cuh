@@ -214,10 +214,6 @@ __device__ __forceinline__ NbrList<T, EXT, POW> load_nbrs(const Dev<T>& C, int i
 // the error margin).  Returns 1 if outside; *wit gets the closer site with the
 // smallest (f_k, k) among the certified ones.
 // ---------------------------------------------------------------------------
-struct CornerScratch {
-  int pad;
-};
-
 template <typename T, typename NL, typename Exact>
 __device__ int corner_outside(const Dev<T>& C, int i, T vix, T viy, T viz, T qx, T qy, T qz, T e,
                               const int* excl, int lane, ScanScratch& S, const NL& L, Exact& exact,
