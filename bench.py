@@ -1,5 +1,5 @@
 #!/usr/bin/env python
-"""Benchmark: clipped Voronoi cells per second on one B300 (or N replicas).
+"""Benchmark: clipped Voronoi cells per second on one B300 (or one diagram over N).
 
 One step = one ``vd_compute`` through the C ABI: grid build, nearest-neighbour
 distances, seeding, the persistent clip-and-flood kernel and the per-site
@@ -17,8 +17,11 @@ cpu_baseline  the FP64 CPU oracle on the whole workload (all host threads; one
         result against it (oracle_check) and the paper's serial method on one
         thread (serial_baseline).
 
-Multi-GPU (torchrun): independent replicas (different seeds), no data-path
-collective; value = cells of all ranks / max over ranks of the step time.
+Multi-GPU (torchrun): one diagram partitioned across the ranks by site
+ownership (Morton ranges; paper_2509_07175_b300/parallel.py).  A step is the
+partitioned compute with its pair exchange (gathers over NCCL until no rank
+sends a pair); value = the workload's cells / max over ranks of the step time
+(strong scaling).
 """
 from __future__ import annotations
 
@@ -140,13 +143,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def replica_seed(rank: int):
-    """Seed of rank's instance: rank 0 runs the workload's own seed, every other
-    rank an independent seeded instance of the same recipe (replicas, weak scaling)."""
-    from paper_2509_07175_b300 import inputs as I
-    return None if rank == 0 else I.SEED_BASE + 1000 + rank
-
-
 def reduce_over_ranks(dist, maxes, sums, device):
     """Element-wise MAX of `maxes` and SUM of `sums` over all ranks (no-op without
     a process group).  Used for the step time (max over ranks) and the counts."""
@@ -160,9 +156,10 @@ def reduce_over_ranks(dist, maxes, sums, device):
     return tm.tolist(), ts.tolist()
 
 
-def whole_job_rate(units_per_rank: int, steps: int, world: int, max_ms: float) -> float:
-    """Units of all ranks per second of the slowest rank."""
-    return units_per_rank * steps * world / (max_ms / 1e3)
+def whole_job_rate(units: int, steps: int, max_ms: float) -> float:
+    """Units of the whole job (one diagram of `units` cells per step, however many
+    ranks share it) per second of the slowest rank."""
+    return units * steps / (max_ms / 1e3)
 
 
 def cpu_model():
@@ -318,7 +315,7 @@ def run_reference(args, rank, world):
     base = {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"each step: all pieces of {k} random sites of the {n} ({ms / 1e3:.2f} s)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "desc": DESC.get(args.workload), "n_sites": n,
                        "n_simplices": len(w["simp"]), "sites_per_step": k},
@@ -367,7 +364,7 @@ def main():
         # produces for seeded 100k-site cube instances (outside the timed region)
         from paper_2509_07175_b300 import learned as L
         training = L.trained_state(mix=L.MIX)
-    w = I.workload(args.workload, seed=replica_seed(rank))
+    w = I.workload(args.workload)
     n = len(w["sites"])
     d = B.diagram_from_workload(w)
     if mlp:
@@ -395,19 +392,34 @@ def main():
             L.load_state(d, training["state"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.current_stream()
+    owner_t = ex = None
+    if world > 1:
+        # one diagram across the ranks: each computes the cells of its own sites
+        from paper_2509_07175_b300 import parallel as P
+        owner_t = torch.tensor(P.morton_owner(w["sites"], world), device="cuda")
+        d.set_partition(owner_t, rank)
+        ex = P.DistExchange(dist, rank, world, "cuda")
+
+    def step():
+        """One step: (status, clip-phase ms, kernels launched)."""
+        if ex is None:
+            code, r = d.compute_raw()
+            return code, r.phase_ms[3], int(r.stats[13])
+        res, _rounds = P.compute(d, owner_t, ex)
+        return res["status"], res["phase_ms"]["clip"], int(res["stats"].get("launches", 0))
 
     def time_form(opts, steps, warm=2):
         """Median ms per step of a form (L2 flushed before each step, CUDA events)."""
         d.set_options(**opts)
         for _ in range(warm):
-            code, _r = d.compute_raw()
+            code = step()[0]
             assert code == 0, B.ERRORS.get(code, code)
         ms = []
         for k in range(steps):
             flush.fill_(float(k))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            code, _r = d.compute_raw()
+            code = step()[0]
             e1.record(stream)
             torch.cuda.synchronize()
             assert code == 0, B.ERRORS.get(code, code)
@@ -448,7 +460,7 @@ def main():
     d.set_options(timing=1, mapping=0, **form)
     tune = d.autotune()
     for _ in range(args.warmup):
-        code, _r = d.compute_raw()
+        code = step()[0]
         assert code == 0, B.ERRORS.get(code, code)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -463,11 +475,11 @@ def main():
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
-        code, r = d.compute_raw()
+        code, cms, nl = step()
         ends[k].record(stream)
         assert code == 0, B.ERRORS.get(code, code)
-        clip_ms.append(r.phase_ms[3])
-        launches += int(r.stats[13])
+        clip_ms.append(cms)
+        launches += nl
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -475,7 +487,8 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     (total_ms,), (launches,) = reduce_over_ranks(dist, [sum(step_ms)], [launches], "cuda")
     launches = int(launches)
-    value = whole_job_rate(n, args.steps, world, total_ms)
+    # one diagram of n cells per step, over the slowest rank's time
+    value = whole_job_rate(n, args.steps, total_ms)
 
     # end to end through the public API with host buffers
     dim = 2 if w["mode"] == B.MODE_2D else 3
@@ -489,7 +502,7 @@ def main():
     d.set_options(**form)
     for _ in range(2):
         d.update_sites_host(host_sites)
-        d.compute_raw()
+        step()
         d.copy_result_host(meas_h, cen_h, off_h, idx_h)
     if dist:
         dist.barrier()
@@ -497,12 +510,12 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         d.update_sites_host(host_sites)
-        code, _r = d.compute_raw()
+        step()
         d.copy_result_host(meas_h, cen_h, off_h, idx_h)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     (e2e_s,), _ = reduce_over_ranks(dist, [e2e_s], [], "cuda")
-    e2e_val = whole_job_rate(n, args.steps, world, e2e_s * 1e3)
+    e2e_val = whole_job_rate(n, args.steps, e2e_s * 1e3)
     esz = 8 if w["f64"] else 4
     h2d = n * dim * esz
     d2h = n * esz + 3 * n * esz + (n + 1) * 8 + nnz * 4
@@ -529,13 +542,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w["f64"] else "f32", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64" if w["f64"] else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": DESC[args.workload], "n_sites": n,
                    "n_simplices": len(w["simp"]), "pairs": counts["pairs"], "nonempty_pieces": counts["nonempty"],
                    "split": ({"whole_cells": counts["whole_cells"], "boundary_sites": counts["boundary_sites"]}
                              if split else None),
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"site partition x{world} (Morton ranges)" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_flood<float, 3D> (Alg. 3 clip + flood)", "bound": "alu", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "peak_source": f"{sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",

@@ -280,6 +280,40 @@ int vd_get_status(vd_ctx* ctx, int* status);
  * No synchronisation.  VD_ERR_STATE before any status was read. */
 int vd_get_result(vd_ctx* ctx, vd_result* out);
 
+/* Partition of one diagram across ranks (one context per rank, each on its
+ * own GPU).  The pieces P_{a,i} are independent (Sec. 4: "no inter-thread
+ * synchronisation"), so every rank computes the pieces of the sites it owns:
+ * owner (device int32[n], copied) gives the rank of each site and rank is this
+ * context's.  Seeding pushes only owned sites' pairs (each rank seeds its own,
+ * Alg. 4 / Alg. 5; the split's boundary pass runs whole on every rank); a pair
+ * (T, j) that the flood finds for a site j of another rank (a positive flag,
+ * Alg. 4) goes once to this rank's outbox instead of its queue.  After
+ * vd_compute the caller sends each outbox key to the owner of its site and
+ * hands what it receives to vd_resume, until no rank has outgoing pairs; the
+ * per-site results of a rank are then final for its sites (measure 0 and no
+ * neighbours elsewhere).  owner NULL: one rank owns all sites (the default).
+ * Errors: VD_ERR_ARG (rank < 0), VD_ERR_STATE (before vd_set_domain or while a
+ * vd_compute_async is pending), VD_ERR_OOM.  vd_lloyd refuses a partitioned
+ * context (an iteration needs the exchange of pairs and of the moved sites). */
+int vd_set_partition(vd_ctx* ctx, const int32_t* owner, int rank);
+
+/* The pairs for other ranks found by the last vd_compute / vd_resume: *keys
+ * (device, owned by the context, valid until the next compute or resume) holds
+ * *count keys (simplex << 32) | site, each at most once per computation.
+ * *count is 0 without a partition.  VD_ERR_STATE before a computation. */
+int vd_get_outbox(vd_ctx* ctx, const uint64_t** keys, int64_t* count);
+
+/* Continue the last computation with pairs received from other ranks: keys
+ * (device uint64[count], (simplex << 32) | site, caller-owned, read before the
+ * call returns) enter the pair set; the new ones are clipped and flooded like
+ * seeds, the outbox restarts with what they lead to, and the per-site
+ * reduction (Sec. 2.1) is redone over all pieces.  *added (may be NULL)
+ * receives the number of new pairs; out (may be NULL) is filled as by
+ * vd_compute.  Synchronises.  Errors: VD_ERR_ARG (a key outside the domain or
+ * the sites, also as the device status), VD_ERR_STATE (no successful
+ * computation to continue), the device-side codes of vd_compute. */
+int vd_resume(vd_ctx* ctx, const uint64_t* keys, int64_t count, int64_t* added, vd_result* out);
+
 /* Autotune the clip kernel now on the current sites (batching, Sec. 4.3: one
  * persistent launch drains the pair queue): runs vd_compute's work once per
  * candidate -- one warp or one thread per pair (3D FP32 tetrahedra without the

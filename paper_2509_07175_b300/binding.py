@@ -99,6 +99,9 @@ def load(path: str = LIB_PATH):
         "vd_set_box": ([P, P, P], I),
         "vd_create_power2d": ([ctypes.POINTER(P), P, P, I64], I),
         "vd_set_weights": ([P, P], I),
+        "vd_set_partition": ([P, P, I], I),
+        "vd_get_outbox": ([P, ctypes.POINTER(P), ctypes.POINTER(I64)], I),
+        "vd_resume": ([P, P, I64, ctypes.POINTER(I64), ctypes.POINTER(Result)], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -117,7 +120,7 @@ def exported_symbols():
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
             "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box",
             "vd_create_power2d", "vd_compute_async", "vd_get_status", "vd_get_result", "vd_model_save",
-            "vd_model_load", "vd_set_weights"]
+            "vd_model_load", "vd_set_weights", "vd_set_partition", "vd_get_outbox", "vd_resume"]
 
 
 class _DevArray:
@@ -258,6 +261,34 @@ class Diagram:
             _check(int(r.status), "device status")
         self.result = r
         return self._pack(r, int(r.status))
+
+    def set_partition(self, owner, rank):
+        """Own the sites with owner[i] == rank (owner: int32 tensor [n]); None: own all."""
+        if owner is None:
+            _check(load().vd_set_partition(self._h, None, 0), "vd_set_partition")
+            return
+        o = owner.to(device="cuda", dtype=torch.int32).contiguous()
+        _check(load().vd_set_partition(self._h, o.data_ptr(), int(rank)), "vd_set_partition")
+
+    def outbox(self):
+        """Pairs found for other ranks' sites (int64 keys (simplex << 32) | site, a copy)."""
+        k, cnt = ctypes.c_void_p(), ctypes.c_int64()
+        _check(load().vd_get_outbox(self._h, ctypes.byref(k), ctypes.byref(cnt)), "vd_get_outbox")
+        n = int(cnt.value)
+        if n == 0:
+            return torch.zeros(0, dtype=torch.int64, device="cuda")
+        return _view(k.value, (n,), torch.int64).clone()
+
+    def resume(self, keys, check=True):
+        """Continue the computation with received pairs; returns (result, new pairs)."""
+        kk = keys.to(device="cuda", dtype=torch.int64).contiguous()
+        r, added = Result(), ctypes.c_int64()
+        code = load().vd_resume(self._h, kk.data_ptr() if kk.numel() else None, int(kk.numel()),
+                                ctypes.byref(added), ctypes.byref(r))
+        if check:
+            _check(code, "vd_resume")
+        self.result = r
+        return self._pack(r, code), int(added.value)
 
     def model_save(self, path):
         _check(load().vd_model_save(self._h, os.fsencode(path)), "vd_model_save")

@@ -132,6 +132,15 @@ struct vd_ctx {
   int* lift_scratch = nullptr;  // [3]: ordered max weight, ordered max lift, bad-weight flag
   float lift_max = 0.f;
   bool lift_on = false;
+  // partition of one diagram across ranks (vd_set_partition)
+  int* owner = nullptr;            // [n] rank of each site
+  int part_rank = 0;
+  bool part_on = false;
+  unsigned long long* outbox = nullptr;
+  long long ocap = 0;
+  long long last_out = 0;          // pairs in the outbox after the last compute / resume
+  unsigned long long* push_keys = nullptr;  // vd_resume: the received pairs, copied
+  long long push_cap = 0;
   cudaGraphExec_t gexec = nullptr;
   int graph_iters = 0;         // Lloyd iterations held by the captured graph
   cudaGraph_t graph = nullptr;
@@ -250,6 +259,10 @@ static Dev<T> make_dev(vd_ctx* c) {
   D.split = split_active(c) ? 1 : 0;
   if (D.split)
     for (int d = 0; d < 3; ++d) { D.blo[d] = c->mlo[d]; D.bhi[d] = c->mhi[d]; }
+  D.owner = c->part_on ? c->owner : nullptr;
+  D.rank = c->part_rank;
+  D.outbox = c->outbox;
+  D.ocap = c->ocap;
   return D;
 }
 
@@ -284,6 +297,54 @@ static size_t scan_tmp_elems(long long n) {
 // everything of one diagram computation, enqueued on c->stream (graph-capturable)
 static inline void mark(vd_ctx* c, int k) {
   if (c->timing_now) cudaEventRecord(c->ev[k], c->stream);
+}
+
+// the clip kernel over the queue (persistent; mapping and list size as resolved)
+template <typename T, int MODE>
+static void enqueue_flood(vd_ctx* c, const Dev<T>& D) {
+  cudaStream_t s = c->stream;
+  bool thread_form = false;
+  if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) thread_form = c->cur_mapping == 2;
+  if (thread_form) {
+    if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value)
+      k_flood_thread<<<c->flood_grid_t, FLOOD_T_THREADS, 0, s>>>(D, c->cur_chunk);
+  } else {
+    bool power = false;
+    if constexpr (std::is_same<T, float>::value && MODE != VD_MODE_2D) {
+      if (D.lift) {
+        k_flood<T, MODE, false, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+        power = true;
+      }
+    }
+    if (power) {
+    } else if (D.knn2) {
+      k_flood<T, MODE, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+    } else {
+      k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
+    }
+  }
+  c->launches += 1;
+}
+
+// per-site reduction of the pieces and the neighbour CSR
+template <typename T, int MODE>
+static void enqueue_reduce(vd_ctx* c, const Dev<T>& D) {
+  cudaStream_t s = c->stream;
+  cudaMemsetAsync(c->scnt, 0, sizeof(int) * (c->n + 1), s);
+  cudaMemsetAsync(c->scur, 0, sizeof(int) * c->n, s);
+  cudaMemsetAsync(c->fc, 0, sizeof(int) * (c->n + 1), s);
+  cudaMemsetAsync(c->ucnt, 0, sizeof(int) * (c->n + 1), s);
+  unsigned pg = (unsigned)std::max(1, c->nsm * 8);
+  k_site_count<T><<<pg, 256, 0, s>>>(D, c->scnt);
+  scan_excl<int, int>(s, c->scnt, c->soff, c->n + 1, (int*)c->scan_tmp);
+  k_site_fill<T><<<pg, 256, 0, s>>>(D, c->soff, c->scur, c->slist);
+  unsigned bs = nblk(c->n, 128);
+  k_site_reduce<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, (T*)c->measure, (T*)c->centroid, c->fc);
+  scan_excl<int, int>(s, c->fc, c->foff, c->n + 1, (int*)c->scan_tmp);
+  k_site_nbr<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, c->foff, c->tmp, c->ucnt);
+  scan_excl<int, long long>(s, c->ucnt, c->noff, c->n + 1, (long long*)c->scan_tmp);
+  k_site_nbr_copy<<<bs, 128, 0, s>>>((int)c->n, c->foff, c->tmp, c->noff, c->nidx, c->status);
+  c->launches += 5 + 3 * scan_launches(c->n + 1);
 }
 
 template <typename T, int MODE>
@@ -344,6 +405,7 @@ static void enqueue_compute(vd_ctx* c) {
       Dev<float> S = D;
       S.mode = VD_MODE_SURFACE; S.m = (int)c->mb; S.k = 3; S.simp = c->bsimp; S.adj = c->badj;
       S.fsgn = nullptr; S.tsgn = nullptr; S.want_stats = 0; S.split = 0; S.box = 0;
+      S.owner = nullptr;  // every rank runs the whole boundary pass; seeds are filtered below
       if (c->nlev > 1) S.G.qlev = c->qlev_nbr;  // boundary points: level of the densest neighbour
       unsigned pg = (unsigned)std::max(1, c->nsm * 8);
       unsigned long long* seeds = (unsigned long long*)c->pm1;  // free until the 3D flood writes it
@@ -369,44 +431,22 @@ static void enqueue_compute(vd_ctx* c) {
     c->launches += MODE != VD_MODE_SURFACE ? 2 : 1;
   }
   mark(c, 3);
-  bool thread_form = false;
-  if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value) thread_form = c->cur_mapping == 2;
-  if (thread_form) {
-    if constexpr (MODE == VD_MODE_3D && std::is_same<T, float>::value)
-      k_flood_thread<<<c->flood_grid_t, FLOOD_T_THREADS, 0, s>>>(D, c->cur_chunk);
-  } else {
-    bool power = false;
-    if constexpr (std::is_same<T, float>::value && MODE != VD_MODE_2D) {
-      if (D.lift) {
-        k_flood<T, MODE, false, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
-        power = true;
-      }
-    }
-    if (power) {
-    } else if (D.knn2) {
-      k_flood<T, MODE, true><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
-    } else {
-      k_flood<T, MODE><<<c->flood_grid, FLOOD_WARPS * 32, c->flood_smem, s>>>(D, c->cur_chunk);
-    }
-  }
-  c->launches += 1;
+  enqueue_flood<T, MODE>(c, D);
   mark(c, 4);
-  cudaMemsetAsync(c->scnt, 0, sizeof(int) * (c->n + 1), s);
-  cudaMemsetAsync(c->scur, 0, sizeof(int) * c->n, s);
-  cudaMemsetAsync(c->fc, 0, sizeof(int) * (c->n + 1), s);
-  cudaMemsetAsync(c->ucnt, 0, sizeof(int) * (c->n + 1), s);
-  unsigned pg = (unsigned)std::max(1, c->nsm * 8);
-  k_site_count<T><<<pg, 256, 0, s>>>(D, c->scnt);
-  scan_excl<int, int>(s, c->scnt, c->soff, c->n + 1, (int*)c->scan_tmp);
-  k_site_fill<T><<<pg, 256, 0, s>>>(D, c->soff, c->scur, c->slist);
-  unsigned bs = nblk(c->n, 128);
-  k_site_reduce<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, (T*)c->measure, (T*)c->centroid, c->fc);
-  scan_excl<int, int>(s, c->fc, c->foff, c->n + 1, (int*)c->scan_tmp);
-  k_site_nbr<T><<<bs, 128, 0, s>>>(D, c->soff, c->slist, c->foff, c->tmp, c->ucnt);
-  scan_excl<int, long long>(s, c->ucnt, c->noff, c->n + 1, (long long*)c->scan_tmp);
-  k_site_nbr_copy<<<bs, 128, 0, s>>>((int)c->n, c->foff, c->tmp, c->noff, c->nidx, c->status);
-  c->launches += 5 + 3 * scan_launches(c->n + 1);
+  enqueue_reduce<T, MODE>(c, D);
   mark(c, 5);
+}
+
+template <typename T, int MODE>
+static void enqueue_resume(vd_ctx* c, const unsigned long long* keys, long long count) {
+  Dev<T> D = make_dev<T>(c);
+  c->launches = 0;
+  k_resume_prep<<<1, 1, 0, c->stream>>>(c->ctr);
+  if (count > 0)
+    k_push_keys<T><<<std::min<unsigned>(nblk(count, 256), (unsigned)c->nsm * 8), 256, 0, c->stream>>>(D, keys, count);
+  c->launches += count > 0 ? 2 : 1;
+  enqueue_flood<T, MODE>(c, D);
+  enqueue_reduce<T, MODE>(c, D);
 }
 
 static void enqueue_any(vd_ctx* c) {
@@ -512,6 +552,7 @@ static int read_status(vd_ctx* c) {
   CK(cudaMemcpy(&nnz, c->noff + c->n, sizeof(long long), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&nonempty, c->soff + c->n, sizeof(int), cudaMemcpyDeviceToHost));
   c->last_pairs = (long long)std::min<unsigned long long>(ctr[CTR_TAIL], (unsigned long long)c->qcap);
+  c->last_out = c->part_on ? (long long)std::min<unsigned long long>(ctr[CTR_OUT], (unsigned long long)c->ocap) : 0;
   c->last_nnz = nnz;
   c->last_nonempty = nonempty;
   c->last_stats[VD_STAT_PAIRS] = (unsigned long long)c->last_pairs;
@@ -1191,6 +1232,54 @@ int vd_get_result(vd_ctx* c, vd_result* out) {
   return VD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// partition of one diagram across ranks
+// ---------------------------------------------------------------------------
+int vd_set_partition(vd_ctx* c, const int32_t* owner, int rank) {
+  if (!c) return VD_ERR_ARG;
+  if (c->pending) return VD_ERR_STATE;
+  c->computed = false;
+  if (!owner) { c->part_on = false; return VD_OK; }
+  if (rank < 0 || !c->have_domain) return rank < 0 ? VD_ERR_ARG : VD_ERR_STATE;
+  if (!c->owner) DALLOC(c->owner, int, c->n, false);
+  if (!c->outbox || c->ocap < c->qcap) {
+    DALLOC(c->outbox, unsigned long long, c->qcap, false);
+    c->ocap = c->qcap;
+  }
+  CK(cudaMemcpyAsync(c->owner, owner, sizeof(int) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->part_rank = rank;
+  c->part_on = true;
+  return VD_OK;
+}
+
+int vd_get_outbox(vd_ctx* c, const uint64_t** keys, int64_t* count) {
+  if (!c || !keys || !count) return VD_ERR_ARG;
+  if (!c->computed || c->pending) return VD_ERR_STATE;
+  *keys = (const uint64_t*)c->outbox;
+  *count = c->part_on ? c->last_out : 0;
+  return VD_OK;
+}
+
+int vd_resume(vd_ctx* c, const uint64_t* keys, int64_t count, int64_t* added, vd_result* out) {
+  if (!c || count < 0 || (count > 0 && !keys)) return VD_ERR_ARG;
+  if (!c->computed || c->pending || c->last_status != VD_OK) return VD_ERR_STATE;
+  CK(cudaMemsetAsync(c->status, 0, 2 * sizeof(int), c->stream));
+  c->timing_now = false;
+  const unsigned long long* k = (const unsigned long long*)keys;
+  if (c->dtype == VD_F64) enqueue_resume<double, VD_MODE_2D>(c, k, count);
+  else if (c->mode == VD_MODE_3D) enqueue_resume<float, VD_MODE_3D>(c, k, count);
+  else if (c->mode == VD_MODE_SURFACE) enqueue_resume<float, VD_MODE_SURFACE>(c, k, count);
+  else enqueue_resume<float, VD_MODE_2D>(c, k, count);
+  CK(cudaGetLastError());
+  int st = read_status(c);
+  unsigned long long ctr[CTR_N];
+  CK(cudaMemcpy(ctr, c->ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+  if (added) *added = (int64_t)(std::min<unsigned long long>(ctr[CTR_TAIL], (unsigned long long)c->qcap) - ctr[CTR_MARK]);
+  fill_result(c, out);
+  return st;
+}
+
 int vd_autotune(vd_ctx* c, int* mapping, int* chunk, float* times_ms) {
   if (!c) return VD_ERR_ARG;
   if (!c->have_domain) return VD_ERR_STATE;
@@ -1219,6 +1308,7 @@ int vd_copy_result_host(vd_ctx* c, void* measure, void* centroid, int64_t* nbr_o
 int vd_lloyd(vd_ctx* c, int iters, int use_graph) {
   if (!c || iters < 0) return VD_ERR_ARG;
   if (!c->have_domain) return VD_ERR_STATE;
+  if (c->part_on) return VD_ERR_STATE;  // a partitioned iteration exchanges pairs and sites between ranks
   if (wants_network(c) && !c->mlp_ready) return VD_ERR_STATE;
   if (iters == 0) return VD_OK;
   if (c->opt.mapping == 0 && !c->tuned) {

@@ -7,7 +7,7 @@
 namespace vd {
 
 // counters in Dev::ctr
-enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_SEEDS = 4, CTR_N = 8 };
+enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_SEEDS = 4, CTR_OUT = 5, CTR_MARK = 6, CTR_N = 8 };
 
 template <typename T>
 struct Dev {
@@ -61,7 +61,19 @@ struct Dev {
   // bounding box) clipped by the site's bisectors; the pieces of per-tetrahedron
   // pairs propagate through negative flags only
   int split;
+  // partition of one diagram across ranks (site ownership): pairs of sites this
+  // rank does not own are recorded in the outbox for their owner instead of being
+  // queued (null owner: one rank owns every site)
+  const int* owner;      // [n] rank of each site, or null
+  int rank;
+  unsigned long long* outbox;
+  long long ocap;
 };
+
+template <typename T>
+__device__ __forceinline__ bool owned(const Dev<T>& C, int i) {
+  return !C.owner || C.owner[i] == C.rank;
+}
 
 __device__ __forceinline__ unsigned long long pair_key(int a, int i) {
   return ((unsigned long long)(unsigned)a << 32) | (unsigned)i;
@@ -83,6 +95,12 @@ __device__ int push_pair(const Dev<T>& C, int a, int i) {
     unsigned long long prev = atomicCAS(C.hash + h, EMPTY_KEY, key);
     if (prev == key) return 0;
     if (prev == EMPTY_KEY) {
+      if (!owned(C, i)) {  // another rank's pair: to the outbox, once (the pair set dedups)
+        unsigned long long o = atomicAdd(C.ctr + CTR_OUT, 1ull);
+        if ((long long)o >= C.ocap) { set_error(C.status, VD_ERR_CAPACITY); return 0; }
+        C.outbox[o] = key;
+        return 0;
+      }
       unsigned long long pos = atomicAdd(C.ctr + CTR_TAIL, 1ull);
       if ((long long)pos >= C.qcap) { set_error(C.status, VD_ERR_CAPACITY); return 0; }
       C.queue[pos] = key;

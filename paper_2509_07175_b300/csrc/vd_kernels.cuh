@@ -153,7 +153,7 @@ __global__ void k_seed_simplex(const __grid_constant__ Dev<T> C) {
   T d2;
   // power diagrams: the nearest lifted site, whose power cell contains the centroid
   int i = thread_nearest(C.G, c[0], c[1], c[2], -1, d2, C.lift);
-  if (i >= 0 && i < C.n) push_pair(C, a, i);
+  if (i >= 0 && i < C.n && owned(C, i)) push_pair(C, a, i);  // each rank seeds its own sites
 }
 
 // ---------------------------------------------------------------------------
@@ -205,10 +205,50 @@ __global__ void k_power_heights(const float* w, long long n, int* best, float* l
 // are neighbours and share their grid cells and lists in the caches.
 __global__ void k_seed_box(Dev<float> C) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= C.n) return;
-  if (t == 0) atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)C.n);
-  if ((long long)t >= C.qcap) { set_error(C.status, VD_ERR_CAPACITY); return; }
-  C.queue[t] = pair_key(0, site_id(C.G.L[0].gs[t]));
+  if (!C.owner) {
+    if (t >= C.n) return;
+    if (t == 0) atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)C.n);
+    if ((long long)t >= C.qcap) { set_error(C.status, VD_ERR_CAPACITY); return; }
+    C.queue[t] = pair_key(0, site_id(C.G.L[0].gs[t]));
+    return;
+  }
+  // partitioned: this rank's sites only, compacted a warp at a time (grid order
+  // within each warp)
+  int i = t < C.n ? site_id(C.G.L[0].gs[t]) : -1;
+  bool mine = i >= 0 && owned(C, i);
+  unsigned m = __ballot_sync(FULL, mine);
+  if (!m) return;
+  int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(C.ctr + CTR_TAIL, (unsigned long long)__popc(m));
+  base = __shfl_sync(FULL, base, 0);
+  if (!mine) return;
+  long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
+  if (pos >= C.qcap) { set_error(C.status, VD_ERR_CAPACITY); return; }
+  C.queue[pos] = pair_key(0, i);
+}
+
+// vd_resume: the queue continues from its tail (claims past it by the finished
+// flood are void), the outbox starts empty and the tail before the new pairs is
+// kept to count them
+__global__ void k_resume_prep(unsigned long long* ctr) {
+  unsigned long long t = ctr[CTR_TAIL];
+  ctr[CTR_HEAD] = t;
+  ctr[CTR_DONE] = t;
+  ctr[CTR_OUT] = 0;
+  ctr[CTR_MARK] = t;
+}
+
+// pairs received from the other ranks: into the pair set (new ones are queued)
+template <typename T>
+__global__ void k_push_keys(const __grid_constant__ Dev<T> C, const unsigned long long* keys, long long count) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
+    unsigned long long key = keys[t];
+    long long a = (long long)(key >> 32), i = (long long)(key & 0xffffffffull);
+    // a simplex of the domain (the split's whole cell: m; the box: 0) and a site
+    if (i >= C.n || a > C.m || (C.box && a != 0)) { set_error(C.status, VD_ERR_ARG); continue; }
+    push_pair(C, (int)a, (int)i);
+  }
 }
 
 struct Locator {
@@ -240,6 +280,7 @@ __global__ void k_seed_site(const __grid_constant__ Dev<T> C, Locator L) {
   if (t >= C.n) return;
   const typename Prec<T>::V4 s4 = C.G.L[0].gs[t];  // grid cell order (see k_seed_box)
   int i = site_id(s4);
+  if (!owned(C, i)) return;
   T p[3] = {s4.x, s4.y, s4.z};
   int bx = (int)floor(((double)p[0] - L.ox) * L.ih), by = (int)floor(((double)p[1] - L.oy) * L.ih),
       bz = (int)floor(((double)p[2] - L.oz) * L.ih);
@@ -673,7 +714,7 @@ __global__ void k_split_push(const __grid_constant__ Dev<float> C, const unsigne
   long long ns = (long long)C.ctr[CTR_SEEDS];
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += (long long)gridDim.x * blockDim.x) {
     unsigned long long key = seeds[t];
-    push_pair(C, (int)(key >> 32), (int)(key & 0xffffffffull));
+    if (owned(C, (int)(key & 0xffffffffull))) push_pair(C, (int)(key >> 32), (int)(key & 0xffffffffull));
   }
 }
 
@@ -756,7 +797,7 @@ __global__ void k_split_site(const __grid_constant__ Dev<float> C, Locator L, co
     const float* p = C.sites + 3 * i;
     int bx = (int)floor(((double)p[0] - L.ox) * L.ih), by = (int)floor(((double)p[1] - L.oy) * L.ih),
         bz = (int)floor(((double)p[2] - L.oz) * L.ih);
-    if (bx >= 0 && by >= 0 && bz >= 0 && bx < L.bx && by < L.by && bz < L.bz) {
+    if (owned(C, i) && bx >= 0 && by >= 0 && bz >= 0 && bx < L.bx && by < L.by && bz < L.bz) {
       int b = (bz * L.by + by) * L.bx + bx;
       int t0 = L.start[b], t1 = L.start[b + 1];
       if (!bnd[i])
