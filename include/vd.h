@@ -314,6 +314,14 @@ int vd_get_outbox(vd_ctx* ctx, const uint64_t** keys, int64_t* count);
  * computation to continue), the device-side codes of vd_compute. */
 int vd_resume(vd_ctx* ctx, const uint64_t* keys, int64_t count, int64_t* added, vd_result* out);
 
+/* One Lloyd update (Sec. 6.4) from the last successful computation: every site
+ * whose cell has positive measure moves to its centroid (others stay).  In a
+ * partitioned context only the rank's own sites move (the others have no
+ * pieces here); the caller then assembles the moved sites from their owners
+ * and hands them to vd_update_sites.  Synchronises.  VD_ERR_STATE without a
+ * successful computation since the last update. */
+int vd_lloyd_step(vd_ctx* ctx);
+
 /* Autotune the clip kernel now on the current sites (batching, Sec. 4.3: one
  * persistent launch drains the pair queue): runs vd_compute's work once per
  * candidate -- one warp or one thread per pair (3D FP32 tetrahedra without the

@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "vd_set_partition": ([P, P, I], I),
         "vd_get_outbox": ([P, ctypes.POINTER(P), ctypes.POINTER(I64)], I),
         "vd_resume": ([P, P, I64, ctypes.POINTER(I64), ctypes.POINTER(Result)], I),
+        "vd_lloyd_step": ([P], I),
         "vd_destroy": ([P], None),
         "vd_strerror": ([I], ctypes.c_char_p),
     }
@@ -120,7 +121,8 @@ def exported_symbols():
             "vd_mlp_init", "vd_mlp_set_state", "vd_mlp_get_state", "vd_mlp_features", "vd_mlp_grad",
             "vd_mlp_forward", "vd_mlp_train", "vd_get_candidate_masks", "vd_autotune", "vd_set_box",
             "vd_create_power2d", "vd_compute_async", "vd_get_status", "vd_get_result", "vd_model_save",
-            "vd_model_load", "vd_set_weights", "vd_set_partition", "vd_get_outbox", "vd_resume"]
+            "vd_model_load", "vd_set_weights", "vd_set_partition", "vd_get_outbox", "vd_resume",
+            "vd_lloyd_step"]
 
 
 class _DevArray:
@@ -289,6 +291,10 @@ class Diagram:
             _check(code, "vd_resume")
         self.result = r
         return self._pack(r, code), int(added.value)
+
+    def lloyd_step(self):
+        """Move every site with a non-empty cell to its centroid (the last computation's)."""
+        _check(load().vd_lloyd_step(self._h), "vd_lloyd_step")
 
     def model_save(self, path):
         _check(load().vd_model_save(self._h, os.fsencode(path)), "vd_model_save")

@@ -1280,6 +1280,17 @@ int vd_resume(vd_ctx* c, const uint64_t* keys, int64_t count, int64_t* added, vd
   return st;
 }
 
+int vd_lloyd_step(vd_ctx* c) {
+  if (!c) return VD_ERR_ARG;
+  if (!c->computed || c->pending || c->last_status != VD_OK) return VD_ERR_STATE;
+  enqueue_lloyd(c);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  c->sites_fresh = c->knn_fresh = false;
+  c->computed = false;
+  return VD_OK;
+}
+
 int vd_autotune(vd_ctx* c, int* mapping, int* chunk, float* times_ms) {
   if (!c) return VD_ERR_ARG;
   if (!c->have_domain) return VD_ERR_STATE;

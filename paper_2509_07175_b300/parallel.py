@@ -174,3 +174,44 @@ def merge(results, owner: torch.Tensor):
         within = torch.arange(tot, device=dev) - torch.repeat_interleave(torch.cumsum(c, 0) - c, c)
         idx[off[sites][seg] + within] = r["nbr_idx"][r["nbr_off"][sites][seg] + within]
     return {"measure": measure, "centroid": centroid, "nbr_off": off, "nbr_idx": idx}
+
+
+def _assemble_sites(moved, owner):
+    """The sites as their owners moved them: rank r's copy supplies the rows it owns."""
+    own = owner.to(moved[0].device).long()
+    ar = torch.arange(own.numel(), device=own.device)
+    return torch.stack(moved)[own, ar]
+
+
+def lloyd_local(diagrams, owner: torch.Tensor, iters: int):
+    """Lloyd iterations (Sec. 6.4) of a partitioned diagram whose ranks are
+    contexts of this process: per iteration the partitioned compute, each rank's
+    update of its own sites (vd_lloyd_step), and the moved sites assembled from
+    their owners into every rank (vd_update_sites)."""
+    rounds = []
+    for _ in range(iters):
+        _rs, rd = compute_local(diagrams, owner)
+        rounds.append(rd)
+        moved = []
+        for d in diagrams:
+            d.lloyd_step()
+            moved.append(d.sites())
+        sites = _assemble_sites(moved, owner)
+        for d in diagrams:
+            d.update_sites(sites[:, :d.dim])
+    return rounds
+
+
+def lloyd(d, owner: torch.Tensor, ex: DistExchange, iters: int):
+    """The same with one rank per process: the moved sites travel in one
+    all-reduce of the owners' rows (12 B per site per iteration in FP32)."""
+    own = (owner.to("cuda") == ex.rank)
+    rounds = []
+    for _ in range(iters):
+        _r, rd = compute(d, owner, ex)
+        rounds.append(rd)
+        d.lloyd_step()
+        s = d.sites()
+        part = torch.where(own[:, None], s, torch.zeros_like(s))
+        d.update_sites(ex.sum_(part).to("cuda")[:, :d.dim])
+    return rounds

@@ -105,3 +105,21 @@ def test_resume_rejects_bad_keys_and_lloyd(gpu):
         assert torch.equal(r0[k], r1[k]), k
     for d in ds:
         d.close()
+
+
+@pytest.mark.parametrize("name,n,opts", [("cube", 5000, dict(mapping=1)),
+                                         ("shell", 20000, dict(learned=1, topk=24, split=1, mapping=1))])
+def test_partitioned_lloyd(gpu, name, n, opts):
+    """Lloyd iterations (Sec. 6.4) over two ranks: each rank moves its own sites
+    (vd_lloyd_step) and the moved sites are assembled from their owners; the
+    trajectory equals one context's vd_lloyd bit for bit."""
+    w = I.workload(name, n=n)
+    one = B.diagram_from_workload(w, options=opts)
+    one.lloyd(3, use_graph=False)
+    want = one.sites()
+    one.close()
+    ds, owner = _ranks(w, opts, 2)
+    P.lloyd_local(ds, owner, 3)
+    for d in ds:
+        assert torch.equal(d.sites(), want)
+        d.close()

@@ -26,7 +26,7 @@ def _key(a, i):
 class FakeDiagram:
     """Pairs (a, i) of a small graph: pair (a, i) leads to (a, i + 1) and to
     (a + 1, i) (positive and negative flags of a piece).  Seeds: (0, i) for every
-    owned site i, and (a, 0) for a in 0..m-1 when rank 0 owns site 0."""
+    owned site i."""
 
     def __init__(self, n, m, owner, rank):
         self.n, self.m, self.owner, self.rank = n, m, owner, rank
@@ -99,7 +99,11 @@ def _rank_main(rank, world, port, q):
     # the whole loop on the stand-in context
     fd = FakeDiagram(n, m, owner, rank)
     _r, rounds = PP.compute(fd, owner, ex)
-    q.put((rank, maxes, sums, sorted(got.tolist()), total, sorted(fd.clipped), rounds))
+    # the moved sites of a partitioned Lloyd step: each rank's own rows, summed
+    full = torch.arange(3 * n, dtype=torch.float32).view(n, 3) * 0.5
+    part = torch.where((owner == rank)[:, None], full, torch.zeros_like(full))
+    assembled = torch.equal(ex.sum_(part), full)
+    q.put((rank, maxes, sums, sorted(got.tolist()), total, sorted(fd.clipped), rounds, assembled))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -123,7 +127,8 @@ def test_gloo_ranks_exchange_and_flood(world):
         assert maxes == [100.0 + 10 * (world - 1)]
         assert sums == [sum(7 + r for r in range(world))]
     everything = set()
-    for rank, _m, _s, got, total, clipped, rounds in out:
+    for rank, _m, _s, got, total, clipped, rounds, assembled in out:
+        assert assembled
         assert total == world * n
         want = sorted(_key(a, i) for a in range(world) for i in range(n) if owner[i] == rank)
         assert got == want
