@@ -213,7 +213,7 @@ __device__ __noinline__ float4 refine64(const Dev<float>& C, int a, int i, int s
 }
 
 // ----- exact side tests ----------------------------------------------------------
-__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4, int* unsure = nullptr) {
+__device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int a, int i, int t, int src4) {
   ePlane p[4];
   uchar4 v = W.tv[t];
   // the corner lies on each of its own planes: the side value is exactly zero
@@ -226,14 +226,16 @@ __device__ __noinline__ int exact_side(const Dev<float>& C, const Warp3& W, int 
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
-    if (unsure) *unsure = 1;  // positivity then follows the measures (see process_pair)
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, W.psrc[v.x], W.psrc[v.y], W.psrc[v.z], src4, tie, 0);
+    return s < 0 ? -2 : 2;  // not certified: +-2 (a tie counts as inside)
   }
   return s;
 }
 
-// side of corner t w.r.t. plane P (slot pl): -1 outside, +1 inside, 0 tie (inside)
+// side of corner t w.r.t. plane P (slot pl): -1 outside, +1 inside, 0 on it; +-2 a
+// decision that is a tie (+2, inside) or left uncertain, after which the pair's
+// positivity follows the computed measures
 __device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int a, int i, int t, int pl) {
   float4 q = W.tq[t];
   float4 P = W.pn[pl];
@@ -245,7 +247,9 @@ __device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int 
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return exact_side(C, W, a, i, t, W.psrc[pl], &W.tied);
+  int r = exact_side(C, W, a, i, t, W.psrc[pl]);
+  if (r == 2 || r == -2) W.tied = 1;
+  return r;
 }
 
 // ----- one pair ------------------------------------------------------------------
@@ -874,8 +878,12 @@ __device__ void process_pair(const Dev<float>& C, Warp3& W, int a, int i, long l
       int ex[3];
       ex[0] = W.psrc[v.x]; ex[1] = W.psrc[v.y]; ex[2] = W.psrc[v.z];
       for (int u = 0; u < 3; ++u) if (ex[u] < 0) ex[u] = -2;  // tet faces exclude no site
-      int uns = 0;
-      auto exact = [&](int k) { return exact_side(C, W, a, i, t, k, &uns); };
+      bool uns = false;
+      auto exact = [&](int k) {
+        int r = exact_side(C, W, a, i, t, k);
+        uns |= r == 2 || r == -2;
+        return r;
+      };
       int wit;
       int sc = 0, ls = 0;
       int out = corner_outside(C, i, vi.x, vi.y, vi.z, q.x, q.y, q.z, q.w, ex, lane, W.S, L, exact, &wit, &sc, &ls);

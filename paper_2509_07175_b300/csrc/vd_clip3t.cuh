@@ -158,7 +158,7 @@ __device__ int t_nn_search(const Dev<float>& C, const TList& L, int i, float3 vi
 }
 
 // ----- exact side test -------------------------------------------------------------
-__device__ __noinline__ int t_exact_side(const Dev<float>& C, const Poly& P, int a, int i, int t, int src4, int* unsure = nullptr) {
+__device__ __noinline__ int t_exact_side(const Dev<float>& C, const Poly& P, int a, int i, int t, int src4) {
   unsigned v = P.tv[t];
   int s0 = P.psrc[b0(v)], s1 = P.psrc[b1(v)], s2 = P.psrc[b2(v)];
   if (src4 == s0 || src4 == s1 || src4 == s2) return 0;
@@ -171,9 +171,9 @@ __device__ __noinline__ int t_exact_side(const Dev<float>& C, const Poly& P, int
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
-    if (unsure) *unsure = 1;  // positivity then follows the measures (see process_pair)
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, s0, s1, s2, src4, tie, 0);
+    return s < 0 ? -2 : 2;  // not certified: +-2 (a tie counts as inside)
   }
   return s;
 }
@@ -189,7 +189,9 @@ __device__ __forceinline__ int t_side_of(const Dev<float>& C, const Poly& P, int
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return t_exact_side(C, P, a, i, t, P.psrc[pl], &P.tied);
+  int r = t_exact_side(C, P, a, i, t, P.psrc[pl]);
+  if (r == 2 || r == -2) P.tied = 1;
+  return r;
 }
 
 // ----- point-in-cell test of a corner (Sec. 3.1; same criterion as the warp form) ---
@@ -221,7 +223,12 @@ __device__ __noinline__ int t_corner_outside(const Dev<float>& C, const Poly& P,
   K.nn++;
   // a tie (or an uncertain sign) met by a corner found inside puts it on that
   // site's bisector: the pair's polytope may be degenerate there
-  int uns = 0;
+  bool uns = false;
+  auto exact = [&](int k) {
+    int r = t_exact_side(C, P, a, i, t, k);
+    uns |= r == 2 || r == -2;
+    return r;
+  };
   // 32-NN list certificate (learned form)
   if (L.r32 > 0.f && (double)L.r32 >= 2.0 * ((double)di + (double)delta) * (1.0 + 1e-5) + 1e-30) {
     K.list++;
@@ -235,7 +242,7 @@ __device__ __noinline__ int t_corner_outside(const Dev<float>& C, const Poly& P,
       float f = d2 - di2;
       if (f < -B) {
         if (d2 < ld || (d2 == ld && k < lk)) { ld = d2; lk = k; }
-      } else if (f <= B && (d2 < lo || (d2 == lo && k < lok)) && t_exact_side(C, P, a, i, t, k, &uns) < 0) {
+      } else if (f <= B && (d2 < lo || (d2 == lo && k < lok)) && exact(k) < 0) {
         lo = d2; lok = k;
       }
     }
@@ -273,7 +280,7 @@ __device__ __noinline__ int t_corner_outside(const Dev<float>& C, const Poly& P,
     float d2 = dx * dx + dy * dy + dz * dz;
     float f = d2 - di2;
     if (d2 < bd || (d2 == bd && k < bk)) { bd = d2; bk = k; }
-    if (f >= -B && f <= amb && (d2 < od || (d2 == od && k < ok)) && t_exact_side(C, P, a, i, t, k, &uns) < 0) {
+    if (f >= -B && f <= amb && (d2 < od || (d2 == od && k < ok)) && exact(k) < 0) {
       od = d2; ok = k;
     }
   };

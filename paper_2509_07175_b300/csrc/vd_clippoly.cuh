@@ -154,7 +154,7 @@ __device__ __noinline__ typename Prec<T>::V4 refine(const Dev<T>& C, const WarpP
 }
 
 template <typename T>
-__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4, int* unsure = nullptr) {
+__device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int src4) {
   int km = (k + nv - 1) % nv;
   // the corner lies on each of its own planes: the side value is exactly zero
   if (src4 == -1 || src4 == W.psrc[W.ve[km]] || src4 == W.psrc[W.ve[k]]) return 0;
@@ -167,9 +167,9 @@ __device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a
   int s = side_from_planes(p, &certain, &tie);
   atomicAdd(C.stats + VD_STAT_FP64, 1ull);
   if (!certain) {
-    if (unsure) *unsure = 1;  // positivity then follows the measures (see process_pair)
     atomicAdd(C.stats + (tie ? VD_STAT_TIES : VD_STAT_UNCERTAIN), 1ull);
     record_diag(C.stats, a, i, -1, W.psrc[W.ve[km]], W.psrc[W.ve[k]], src4, tie, 0);
+    return s < 0 ? -2 : 2;  // not certified: +-2 (a tie counts as inside)
   }
   return s;
 }
@@ -184,7 +184,9 @@ __device__ __forceinline__ int side_of(const Dev<T>& C, const WarpP<T>& W, int a
     if (s > b) return 1;
     if (s < -b) return -1;
   }
-  return exact_side(C, W, a, i, k, nv, W.psrc[pl], &W.tied);
+  int r = exact_side(C, W, a, i, k, nv, W.psrc[pl]);
+  if (r == 2 || r == -2) W.tied = 1;
+  return r;
 }
 
 struct Counters {
@@ -411,8 +413,12 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       if (ex[0] < 0) ex[0] = -2;
       if (ex[1] < 0) ex[1] = -2;
       int nvv = nv, kk = k;
-      int uns = 0;
-      auto exact = [&](int site) { return exact_side(C, W, a, i, kk, nvv, site, &uns); };
+      bool uns = false;
+      auto exact = [&](int site) {
+        int r = exact_side(C, W, a, i, kk, nvv, site);
+        uns |= r == 2 || r == -2;
+        return r;
+      };
       int wit, sc = 0, ls = 0;
       int out = corner_outside(C, i, vi[0], vi[1], vi[2], q.x, q.y, q.z, q.w, ex, lane, W.S, L, exact, &wit, &sc, &ls);
       // a corner found inside with a tie (or an uncertain sign) lies on that
