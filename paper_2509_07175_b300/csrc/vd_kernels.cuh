@@ -326,15 +326,18 @@ struct WarpOf<float, VD_MODE_3D> {
 };
 
 constexpr int FLOOD_WARPS = 4;
-#ifndef FLOOD_MIN_BLOCKS
-#define FLOOD_MIN_BLOCKS 3
-#endif
+// resident blocks per SM the register allocation aims at: 4 (128 registers) for
+// the 3D form, 5-6 % faster than 3 on the 100k cube and the 5M box and 1 % on
+// the shell despite its spills; 3 (168 registers) for the polygon forms, which
+// lose 4-10 % with fewer registers
+template <int MODE>
+constexpr int flood_min_blocks() { return MODE == VD_MODE_3D ? 4 : 3; }
 
 // Warp per pair: each warp claims `chunk` consecutive queue slots at a time.
 // EXT: point-in-cell tests and searches may use the 33rd..64th nearest (learned
 // form with the extended list).
 template <typename T, int MODE, bool EXT = false, bool POW = false>
-__global__ void __launch_bounds__(FLOOD_WARPS * 32, FLOOD_MIN_BLOCKS) k_flood(const __grid_constant__ Dev<T> C, int chunk) {
+__global__ void __launch_bounds__(FLOOD_WARPS * 32, flood_min_blocks<MODE>()) k_flood(const __grid_constant__ Dev<T> C, int chunk) {
   using W = typename WarpOf<T, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W& w = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
