@@ -574,7 +574,7 @@ def main():
         "clocks": ck,
         "stats": {k: counts[k] for k in ("nn_queries", "corner_tests", "clips", "lambda_steps", "search_steps",
                                          "fp64", "uncertain", "ties", "sites_scanned", "fallback", "learned_hits",
-                                         "list_tests")},
+                                         "list_tests", "bisector_faces", "excess_clips")},
         "form": ("plain (Sec. 3.2 / 5.1 search)" if args.plain else
                  f"learned+batched ({args.proposal} ranking of the 32 nearest, top-{args.topk}; "
                  "output bit-identical to plain)") + ("; Alg. 5 split (interior cells whole)" if split else ""),
