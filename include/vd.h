@@ -140,6 +140,12 @@ typedef struct {
                               radius from the lists (fewer grid scans, a costlier list pass);
                               32 the 32 only; 0 chosen by the autotuner with mapping 0 (64
                               until tuned). */
+  int force_exact;         /* 1: no FP32 filter in the clip -- every side decision of a corner
+                              against a clipping plane, and every new corner, goes through the
+                              float64 path (the exact sign with its error bound, the corner from
+                              its exact planes).  A test of that path (a filter failure forced
+                              from the host): the topology is the same as with 0, measures and
+                              centroids differ by rounding.  Slower; 0 by default. */
 } vd_options;
 
 enum { VD_PROPOSAL_DISTANCE = 0, VD_PROPOSAL_MLP = 1 };

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("max_search", ctypes.c_int), ("max_lambda", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
                 ("timing", ctypes.c_int), ("grid_density", ctypes.c_double), ("topk", ctypes.c_int),
                 ("proposal", ctypes.c_int), ("split", ctypes.c_int),
-                ("nearest", ctypes.c_int)]
+                ("nearest", ctypes.c_int), ("force_exact", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -259,6 +259,7 @@ static Dev<T> make_dev(vd_ctx* c) {
   D.split = split_active(c) ? 1 : 0;
   if (D.split)
     for (int d = 0; d < 3; ++d) { D.blo[d] = c->mlo[d]; D.bhi[d] = c->mhi[d]; }
+  D.force_exact = c->opt.force_exact ? 1 : 0;
   D.owner = c->part_on ? c->owner : nullptr;
   D.rank = c->part_rank;
   D.outbox = c->outbox;

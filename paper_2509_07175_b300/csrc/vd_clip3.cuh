@@ -240,7 +240,7 @@ __device__ __forceinline__ int side_of(const Dev<float>& C, const Warp3& W, int 
   float4 q = W.tq[t];
   float4 P = W.pn[pl];
   float2 M = W.pm[pl];
-  if (q.w < 1e29f) {
+  if (q.w < 1e29f && !C.force_exact) {
     float s = P.w - (P.x * q.x + P.y * q.y + P.z * q.z);
     float qm = fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z)));
     float b = (fabsf(P.x) + fabsf(P.y) + fabsf(P.z)) * q.w + SIDEF * (M.y + M.x * qm);
@@ -513,7 +513,7 @@ __device__ __forceinline__ int clip(const Dev<float>& C, Warp3& W, Masks& Mk, in
     else if (uv.z == y && uv.x == x) W.tn[u].z = (unsigned char)sl;
     else bad = true;
     float4 qc = corner(W.pn[x], W.pm[x], W.pn[y], W.pm[y], Pn, Mn);
-    if (loose(qc))
+    if (loose(qc) || C.force_exact)
       qc = refine64(C, a, i, W.psrc[x], W.psrc[y], W.psrc[pl]);
     W.tq[sl] = qc;
     W.twit[sl] = -1;
@@ -683,7 +683,7 @@ __device__ __forceinline__ void integrate(const Dev<float>& C, Warp3& W, const M
       q = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
     } else {
       q = corner(W.pn[pl[0]], W.pm[pl[0]], W.pn[pl[1]], W.pm[pl[1]], W.pn[pl[2]], W.pm[pl[2]]);
-      if (loose(q)) q = refine64(C, a, i, sr[0], sr[1], sr[2]);
+      if (loose(q) || C.force_exact) q = refine64(C, a, i, sr[0], sr[1], sr[2]);
     }
     W.tq[t] = q;
     key[r] = corner_key(W.prank[pl[0]], W.prank[pl[1]], W.prank[pl[2]]);

@@ -182,7 +182,7 @@ __device__ __forceinline__ int t_side_of(const Dev<float>& C, const Poly& P, int
   float4 q = P.tq[t];
   float4 Pl = P.pn[pl];
   float2 M = P.pm[pl];
-  if (q.w < 1e29f) {
+  if (q.w < 1e29f && !C.force_exact) {
     float s = Pl.w - (Pl.x * q.x + Pl.y * q.y + Pl.z * q.z);
     float qm = fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z)));
     float b = (fabsf(Pl.x) + fabsf(Pl.y) + fabsf(Pl.z)) * q.w + SIDEF * (M.y + M.x * qm);
@@ -459,7 +459,7 @@ __device__ __noinline__ int t_clip(const Dev<float>& C, Poly& P, Masks& Mk, int 
     else { set_error(C.status, VD_ERR_LIMIT); return -1; }
     P.tn[u] = un;
     float4 qc = c3::corner(P.pn[x], P.pm[x], P.pn[y], P.pm[y], Pn, Mn);
-    if (c3::loose(qc))
+    if (c3::loose(qc) || C.force_exact)
       qc = c3::refine64(C, a, i, P.psrc[x], P.psrc[y], P.psrc[pl]);
     P.tq[sl] = qc;
     P.twit[sl] = -1;
@@ -525,7 +525,7 @@ __device__ __noinline__ void t_integrate(const Dev<float>& C, Poly& P, const Mas
         q = make_float4(qx, qy, qz, 2.f * U * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz))));
       } else {
         q = c3::corner(P.pn[pl[0]], P.pm[pl[0]], P.pn[pl[1]], P.pm[pl[1]], P.pn[pl[2]], P.pm[pl[2]]);
-        if (c3::loose(q)) q = c3::refine64(C, a, i, sr[0], sr[1], sr[2]);
+        if (c3::loose(q) || C.force_exact) q = c3::refine64(C, a, i, sr[0], sr[1], sr[2]);
       }
       P.tq[t] = q;
       unsigned long long kk = c3::corner_key(prank[pl[0]], prank[pl[1]], prank[pl[2]]);

@@ -177,7 +177,7 @@ __device__ __noinline__ int exact_side(const Dev<T>& C, const WarpP<T>& W, int a
 template <typename T>
 __device__ __forceinline__ int side_of(const Dev<T>& C, const WarpP<T>& W, int a, int i, int k, int nv, int pl) {
   typename Prec<T>::V4 q = W.vq[k], P = W.pn[pl];
-  if (q.w < T(1e29)) {
+  if (q.w < T(1e29) && !C.force_exact) {
     T s = P.w - (P.x * q.x + P.y * q.y + P.z * q.z);
     T qm = fmax(fabs(q.x), fmax(fabs(q.y), fabs(q.z)));
     T b = (fabs(P.x) + fabs(P.y) + fabs(P.z)) * q.w + sidef<T>() * (W.pmc[pl] + W.pmx[pl] * qm);
@@ -351,11 +351,11 @@ __device__ __forceinline__ int clip(const Dev<T>& C, WarpP<T>& W, int a, int i, 
   typename Prec<T>::V4 X, Y;
   if (lane == keep) {
     X = corner(W, 0, eX, pl);
-    if (sizeof(T) == 4 && !(X.w <= T(3e-3) * sqrt(X.x * X.x + X.y * X.y + X.z * X.z))) X = refine(C, W, a, i, X, eX, pl);
+    if (sizeof(T) == 4 && (C.force_exact || !(X.w <= T(3e-3) * sqrt(X.x * X.x + X.y * X.y + X.z * X.z)))) X = refine(C, W, a, i, X, eX, pl);
   }
   if (lane == keep + 1) {
     Y = corner(W, 0, pl, eY);
-    if (sizeof(T) == 4 && !(Y.w <= T(3e-3) * sqrt(Y.x * Y.x + Y.y * Y.y + Y.z * Y.z))) Y = refine(C, W, a, i, Y, pl, eY);
+    if (sizeof(T) == 4 && (C.force_exact || !(Y.w <= T(3e-3) * sqrt(Y.x * Y.x + Y.y * Y.y + Y.z * Y.z)))) Y = refine(C, W, a, i, Y, pl, eY);
   }
   __syncwarp();
   if (lane < keep) { W.vq[lane] = q; W.ve[lane] = ve; W.vst[lane] = st; W.vwit[lane] = wt; }
@@ -481,7 +481,7 @@ __device__ void process_pair(const Dev<T>& C, WarpP<T>& W, int a, int i, long lo
       } else {
         if (sa + 8 > sb + 8) { int t = pa; pa = pb; pb = t; }
         q = corner(W, 0, pa, pb);
-        if (sizeof(T) == 4 && !(q.w <= T(3e-3) * sqrt(q.x * q.x + q.y * q.y + q.z * q.z))) q = refine(C, W, a, i, q, pa, pb);
+        if (sizeof(T) == 4 && (C.force_exact || !(q.w <= T(3e-3) * sqrt(q.x * q.x + q.y * q.y + q.z * q.z)))) q = refine(C, W, a, i, q, pa, pb);
       }
       unsigned ua = (unsigned)(sa + 8), ub = (unsigned)(sb + 8);
       khi = min(ua, ub);

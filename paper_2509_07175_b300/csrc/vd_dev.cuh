@@ -61,6 +61,7 @@ struct Dev {
   // bounding box) clipped by the site's bisectors; the pieces of per-tetrahedron
   // pairs propagate through negative flags only
   int split;
+  int force_exact;       // 1: every clip decision and new corner through the float64 path
   // partition of one diagram across ranks (site ownership): pairs of sites this
   // rank does not own are recorded in the outbox for their owner instead of being
   // queued (null owner: one rank owns every site)

@@ -190,3 +190,31 @@ def test_corrupted_surface_mesh(gpu, kind):
     assert r["status"] == 0
     compare_full(w, r, d.pieces(), _oracle(w))
     d.close()
+
+
+@pytest.mark.parametrize("name,n,opts", [
+    ("fail", 600, dict(mapping=1)),                      # warp per pair, 3D
+    ("fail", 600, dict(mapping=2)),                      # thread per pair, 3D
+    ("fail", 600, dict(learned=1, topk=16, split=1)),    # learned form with the split
+    ("torus", 3000, dict(mapping=1)),                    # polygon form, surface
+])
+def test_forced_float64_path(gpu, name, n, opts):
+    """A filter failure forced from the host (vd_options.force_exact): every clip
+    decision and every new corner takes the float64 path.  The diagram matches
+    the oracle with the same bar, the neighbours equal the filtered run's, and
+    the float64 count covers the clip decisions."""
+    if name == "fail":
+        w = _cube_case(n)
+    else:  # a small torus (1,600 triangles), sites on it
+        v, s = I.torus_domain(nu=40, nv=20)
+        w = dict(name="torus_small", mode=B.MODE_SURFACE, sites=I.surface_sites(n, v, s, I.SEED_BASE + 0x330),
+                 verts=v, simp=s, f64=False)
+    d = B.diagram_from_workload(w, options=dict(opts, stats=1))
+    ref = d.compute()
+    d.set_options(**dict(opts, stats=1, force_exact=1))
+    r = d.compute()
+    assert r["status"] == 0 and r["stats"]["uncertain"] == 0
+    assert r["stats"]["fp64"] > 3 * ref["stats"]["fp64"]
+    assert torch.equal(r["nbr_off"], ref["nbr_off"]) and torch.equal(r["nbr_idx"], ref["nbr_idx"])
+    compare_full(w, r, d.pieces(), _oracle(w), split=bool(opts.get("split")))
+    d.close()
