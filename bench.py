@@ -366,7 +366,17 @@ def main():
         training = L.trained_state(mix=L.MIX)
     w = I.workload(args.workload)
     n = len(w["sites"])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     d = B.diagram_from_workload(w)
+    # device memory of one context: its inputs, the library's buffers and one
+    # computation's pair set and outputs (cudaMemGetInfo before and after)
+    code, _r = d.compute_raw()
+    assert code == 0, B.ERRORS.get(code, code)
+    torch.cuda.synchronize()
+    device_memory = {"bytes": int(free0 - torch.cuda.mem_get_info()[0]),
+                     "note": "cudaMemGetInfo difference from before the context to after its first compute"}
+    device_memory["bytes_per_site"] = device_memory["bytes"] / n
     if mlp:
         L.load_state(d, training["state"])
     prop = B.PROPOSAL_MLP if mlp else B.PROPOSAL_DISTANCE
@@ -569,6 +579,7 @@ def main():
                                      "null once the kernel sources differ from the captured ones"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "device_memory": device_memory,
         "autotune": {"choice": ("warp" if tune["mapping"] == 1 else "thread") + f" per pair, chunk {tune['chunk']}",
                      "clip_ms_by_candidate": tune["times_ms"]},
         "clocks": ck,
