@@ -123,3 +123,20 @@ def test_partitioned_lloyd(gpu, name, n, opts):
     for d in ds:
         assert torch.equal(d.sites(), want)
         d.close()
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_more_ranks_than_sites(gpu, n):
+    """Four ranks over one or three sites: ranks that own nothing seed nothing
+    and still take part in the exchange; the merged result is the one-context one."""
+    w = I.workload("cube", n=n, seed=I.SEED_BASE + 0x3A0 + n)
+    one = B.diagram_from_workload(w, options=dict(mapping=1))
+    full = one.compute()
+    one.close()
+    ds, owner = _ranks(w, dict(mapping=1), 4)
+    rs, _ = P.compute_local(ds, owner)
+    merged = P.merge(rs, owner)
+    for k in KEYS:
+        assert torch.equal(merged[k], full[k]), k
+    for d in ds:
+        d.close()
