@@ -50,3 +50,29 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.vd_create(ctypes.byref(h), ctypes.c_void_p(16), 0, 3, 0) == -1
     assert lib.vd_create(ctypes.byref(h), ctypes.c_void_p(16), 10, 4, 0) == -1
     assert lib.vd_create(ctypes.byref(h), ctypes.c_void_p(16), 10, 3, 7) == -1
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and field offsets of a struct of include/vd.h, from gcc."""
+    import subprocess
+    src = tmp_path / f"layout_{struct}.c"
+    body = "".join(f'  printf("%s %zu\\n", "{f}", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text(f'#include <stddef.h>\n#include <stdio.h>\n#include "vd.h"\nint main(void) {{\n'
+                   f'  printf("sizeof %zu\\n", sizeof({struct}));\n{body}  return 0;\n}}\n')
+    exe = tmp_path / f"layout_{struct}"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)], text=True).split()
+    return {k: int(v) for k, v in zip(out[::2], out[1::2])}
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """The ctypes mirrors of vd_options, vd_result and vd_pieces have the C layout:
+    the same size and the same offset for every field (a field added on one side
+    only would shift the others silently)."""
+    from paper_2509_07175_b300 import binding as B
+    for struct, cls in (("vd_options", B.Options), ("vd_result", B.Result), ("vd_pieces", B.PiecesC)):
+        names = [f[0] for f in cls._fields_]
+        c = _c_layout(struct, names, tmp_path)
+        assert c["sizeof"] == ctypes.sizeof(cls), struct
+        for name in names:
+            assert c[name] == getattr(cls, name).offset, (struct, name)
