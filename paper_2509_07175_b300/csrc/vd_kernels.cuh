@@ -245,8 +245,9 @@ __global__ void k_push_keys(const __grid_constant__ Dev<T> C, const unsigned lon
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
     unsigned long long key = keys[t];
     long long a = (long long)(key >> 32), i = (long long)(key & 0xffffffffull);
-    // a simplex of the domain (the split's whole cell: m; the box: 0) and a site
-    if (i >= C.n || a > C.m || (C.box && a != 0)) { set_error(C.status, VD_ERR_ARG); continue; }
+    // a simplex of the domain (the box form: 0; the split's whole cell: m) and a site
+    bool ok = i < C.n && (C.box ? a == 0 : (a < C.m || (a == C.m && C.split)));
+    if (!ok) { set_error(C.status, VD_ERR_ARG); continue; }
     push_pair(C, (int)a, (int)i);
   }
 }

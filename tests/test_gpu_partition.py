@@ -89,9 +89,12 @@ def test_resume_rejects_bad_keys_and_lloyd(gpu):
     w = I.workload("cube", n=2000)
     ds, owner = _ranks(w, dict(mapping=1), 2)
     ds[0].compute()
-    with pytest.raises(B.VDError) as e:  # a site index past n
-        ds[0].resume(torch.tensor([(1 << 32) | 5000], dtype=torch.int64, device="cuda"))
-    assert e.value.code == -1
+    for bad in ((1 << 32) | 5000,              # a site index past n
+                (len(w["simp"]) << 32) | 7):   # the whole-cell index m without the split
+        ds[0].compute()
+        with pytest.raises(B.VDError) as e:
+            ds[0].resume(torch.tensor([bad], dtype=torch.int64, device="cuda"))
+        assert e.value.code == -1
     with pytest.raises(B.VDError) as e:  # the partitioned context cannot run Lloyd alone
         ds[1].lloyd(1)
     assert e.value.code == -8
