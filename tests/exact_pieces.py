@@ -99,3 +99,82 @@ def candidates(sites, i, k):
     order = np.argsort(d, kind="stable")
     nb = order[:k]
     return [(int(j), sites[j]) for j in nb], float(d[order[k]]) if k < len(order) - 1 else np.inf
+
+
+def polygon_piece(tri_verts, vi, others):
+    """2D analogue: triangle T (3x2 floats) clipped by the bisectors of vi with
+    the candidate sites, exactly.  Returns (positive area, set of ids whose
+    bisector bounds an edge of positive length, number of triangle edges of
+    positive length)."""
+    tv = [tuple(F(float(x)) for x in v[:2]) for v in tri_verts]
+    fi = tuple(F(float(x)) for x in vi[:2])
+    lines = []  # (n, c, source): n.x <= c
+    for f in range(3):
+        a, b = [tv[k] for k in range(3) if k != f]
+        n = [b[1] - a[1], a[0] - b[0]]
+        c = n[0] * a[0] + n[1] * a[1]
+        if n[0] * tv[f][0] + n[1] * tv[f][1] > c:
+            n, c = [-n[0], -n[1]], -c
+        lines.append((n, c, -1 - f))
+    for j, vj in others:
+        fj = tuple(F(float(x)) for x in vj[:2])
+        n = [fj[0] - fi[0], fj[1] - fi[1]]
+        c = (fj[0] ** 2 + fj[1] ** 2 - fi[0] ** 2 - fi[1] ** 2) / 2
+        lines.append((n, c, int(j)))
+    return _polygon(lines)
+
+
+def surface_piece(tri_verts, vi, others):
+    """Surface: triangle T in 3D (3x3 floats) clipped by the 3D bisectors of vi,
+    exactly, in the triangle's own coordinates p = A + s (B - A) + t (C - A)
+    (an affine map: positive length and area are kept).  Same returns as
+    polygon_piece."""
+    A, Bv, Cv = [tuple(F(float(x)) for x in v) for v in tri_verts]
+    e1 = [Bv[k] - A[k] for k in range(3)]
+    e2 = [Cv[k] - A[k] for k in range(3)]
+    fi = tuple(F(float(x)) for x in vi)
+    # triangle edges opposite vertex 0, 1, 2: s + t <= 1, s >= 0 (-s <= 0), t >= 0
+    lines = [([F(1), F(1)], F(1), -1), ([F(-1), F(0)], F(0), -2), ([F(0), F(-1)], F(0), -3)]
+    for j, vj in others:
+        fj = tuple(F(float(x)) for x in vj)
+        n = [fj[k] - fi[k] for k in range(3)]
+        c = (sum(x * x for x in fj) - sum(x * x for x in fi)) / 2
+        ns = sum(n[k] * e1[k] for k in range(3))
+        nt = sum(n[k] * e2[k] for k in range(3))
+        lines.append(([ns, nt], c - sum(n[k] * A[k] for k in range(3)), int(j)))
+    return _polygon(lines)
+
+
+def _polygon(lines):
+    corners = set()
+    for x, y in combinations(range(len(lines)), 2):
+        (n0, c0, _), (n1, c1, _) = lines[x], lines[y]
+        D = n0[0] * n1[1] - n0[1] * n1[0]
+        if D == 0:
+            continue
+        q = ((c0 * n1[1] - c1 * n0[1]) / D, (n0[0] * c1 - n1[0] * c0) / D)
+        if all(n[0] * q[0] + n[1] * q[1] <= c for n, c, _ in lines):
+            corners.add(q)
+    corners = list(corners)
+
+    def rank2(pts):
+        if not pts:
+            return -1
+        p0 = pts[0]
+        vecs = [(p[0] - p0[0], p[1] - p0[1]) for p in pts[1:]]
+        if all(v == (0, 0) for v in vecs):
+            return 0
+        v0 = next(v for v in vecs if v != (0, 0))
+        return 2 if any(v0[0] * v[1] - v0[1] * v[0] != 0 for v in vecs) else 1
+
+    positive = rank2(corners) == 2
+    edges, tri_edges = set(), 0
+    if positive:
+        for n, c, src in lines:
+            on = [q for q in corners if n[0] * q[0] + n[1] * q[1] == c]
+            if rank2(on) == 1:
+                if src >= 0:
+                    edges.add(src)
+                else:
+                    tri_edges += 1
+    return positive, edges, tri_edges

@@ -73,3 +73,40 @@ def test_shell_slivers(shell, a):
     assert pos
     got = _oracle_pieces(O.Oracle(4, w["sites"], w["verts"], w["simp"]).site_pieces(np.array([i])))
     assert got[(a, i)] == (faces, ntet)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tiny_square_every_piece(seed):
+    """2D: 12 uniform FP64 sites in the unit square as 2 triangles, every
+    (triangle, site) pair computed exactly from all 11 bisectors and the 3 edges."""
+    from exact_pieces import polygon_piece
+    v, s = I.square_grid_tris(1)
+    sites = I.uniform_sites(12, 2, I.SEED_BASE + 0x7F0 + seed, f32=False)
+    got = _oracle_pieces(O.Oracle(2, sites, v, s).enumerate())
+    want = {}
+    for a in range(len(s)):
+        for i in range(len(sites)):
+            pos, edges, ntri = polygon_piece(v[s[a]], sites[i], [(j, sites[j]) for j in range(len(sites)) if j != i])
+            if pos:
+                want[(a, i)] = (edges, ntri)
+    assert set(got) == set(want)
+    for k in want:
+        assert got[k] == want[k], (k, got[k], want[k])
+
+
+def test_tiny_surface_every_piece():
+    """Surface: 10 sites jittered off a small torus mesh (240 triangles), every
+    (triangle, site) pair computed exactly in the triangle's plane."""
+    from exact_pieces import surface_piece
+    v, s = I.torus_domain(nu=12, nv=10)
+    sites = I.surface_sites(10, v, s, I.SEED_BASE + 0x7F8)
+    got = _oracle_pieces(O.Oracle(3, sites, v, s).enumerate())
+    want = {}
+    for a in range(len(s)):
+        for i in range(len(sites)):
+            pos, edges, ntri = surface_piece(v[s[a]], sites[i], [(j, sites[j]) for j in range(len(sites)) if j != i])
+            if pos:
+                want[(a, i)] = (edges, ntri)
+    assert set(got) == set(want)
+    for k in want:
+        assert got[k] == want[k], (k, got[k], want[k])
