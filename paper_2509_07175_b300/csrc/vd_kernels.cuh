@@ -543,6 +543,18 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
   for (long long t = t0 + (threadIdx.x >> 5); t < t1; t += KNN_WARPS) {
     const typename Prec<T>::V4 s4 = C.G.L[0].gs[t];
     const int i = site_id(s4);
+    if (!C.split && !owned(C, i)) {
+      // partitioned without the split: only the rank's own pairs read lists; the
+      // others get empty, uncertified ones (the search then scans the grid)
+      knn[(long long)i * KNN + lane] = -1;
+      knn_d2[(long long)i * KNN + lane] = -1.f;
+      if (knn2) knn2[(long long)i * KNN + lane] = -1;
+      if (lane == 0) {
+        if (knn2) r64[i] = 0.f;
+        if (delta) delta[i] = T(1);
+      }
+      continue;
+    }
     T qx = s4.x, qy = s4.y, qz = s4.z;
     int cnt = 0;
     bool over = false;
