@@ -139,8 +139,7 @@ struct vd_ctx {
   unsigned long long* outbox = nullptr;
   long long ocap = 0;
   long long last_out = 0;          // pairs in the outbox after the last compute / resume
-  unsigned long long* push_keys = nullptr;  // vd_resume: the received pairs, copied
-  long long push_cap = 0;
+  int* own_order = nullptr;        // [n] grid positions of the own sites (nearest-list pass)
   cudaGraphExec_t gexec = nullptr;
   int graph_iters = 0;         // Lloyd iterations held by the captured graph
   cudaGraph_t graph = nullptr;
@@ -262,6 +261,7 @@ static Dev<T> make_dev(vd_ctx* c) {
   D.force_exact = c->opt.force_exact ? 1 : 0;
   D.owner = c->part_on ? c->owner : nullptr;
   D.rank = c->part_rank;
+  D.own_order = (c->part_on && !D.split) ? c->own_order : nullptr;
   D.outbox = c->outbox;
   D.ocap = c->ocap;
   return D;
@@ -384,6 +384,10 @@ static void enqueue_compute(vd_ctx* c) {
   }
   if (lists_active(c)) {
     // learned proposal: the 32 nearest sites, ranked into the candidate list
+    if (D.own_order) {
+      k_own_order<T><<<std::min<unsigned>(nblk(c->n, 256), (unsigned)c->nsm * 16), 256, 0, s>>>(D, D.own_order);
+      c->launches += 1;
+    }
     k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, fused ? (T*)c->delta : nullptr,
                                                      c->cur_list64 ? c->knn2 : nullptr, c->knn_r64);
     if (c->opt.proposal == VD_PROPOSAL_MLP)
@@ -1134,7 +1138,7 @@ static int autotune(vd_ctx* c) {
     if (ms < best_ms) { best_ms = ms; best = k; }
   }
   c->sites_fresh = true;
-  c->knn_fresh = lists_active(c);
+  c->knn_fresh = lists_active(c) && !(c->part_on && !split_active(c));  // partitioned: own sites only
   c->tuned = true;
   c->tuned_mapping = cand_m[best];
   c->tuned_chunk = cand_c[best];
@@ -1195,7 +1199,7 @@ int vd_compute(vd_ctx* c, vd_result* out) {
   c->timing_now = false;
   c->pending = false;
   c->sites_fresh = true;
-  c->knn_fresh = lists_active(c);
+  c->knn_fresh = lists_active(c) && !(c->part_on && !split_active(c));  // partitioned: own sites only
   fill_result(c, out);
   return st;
 }
@@ -1212,7 +1216,7 @@ int vd_compute_async(vd_ctx* c) {
   CK(cudaGetLastError());
   c->pending = true;
   c->sites_fresh = true;
-  c->knn_fresh = lists_active(c);
+  c->knn_fresh = lists_active(c) && !(c->part_on && !split_active(c));  // partitioned: own sites only
   return VD_OK;
 }
 
@@ -1243,6 +1247,7 @@ int vd_set_partition(vd_ctx* c, const int32_t* owner, int rank) {
   if (!owner) { c->part_on = false; return VD_OK; }
   if (rank < 0 || !c->have_domain) return rank < 0 ? VD_ERR_ARG : VD_ERR_STATE;
   if (!c->owner) DALLOC(c->owner, int, c->n, false);
+  if (!c->own_order) DALLOC(c->own_order, int, c->n, false);
   if (!c->outbox || c->ocap < c->qcap) {
     DALLOC(c->outbox, unsigned long long, c->qcap, false);
     c->ocap = c->qcap;
@@ -1574,6 +1579,7 @@ template <typename T>
 int mlp_features_t(vd_ctx* c, void* x, uint32_t* labels) {
   cudaStream_t s = c->stream;
   Dev<T> D = make_dev<T>(c);
+  D.own_order = nullptr;  // the training data lists every site
   if (!c->knn_fresh) {
     k_knn<T><<<c->knn_grid, KNN_WARPS * 32, 0, s>>>(D, c->knn, c->knn_d2, nullptr, nullptr, nullptr);
     c->knn_fresh = true;

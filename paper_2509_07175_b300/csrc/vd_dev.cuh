@@ -7,7 +7,7 @@
 namespace vd {
 
 // counters in Dev::ctr
-enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_SEEDS = 4, CTR_OUT = 5, CTR_MARK = 6, CTR_N = 8 };
+enum { CTR_TAIL = 0, CTR_HEAD = 1, CTR_DONE = 2, CTR_FLAGS = 3, CTR_SEEDS = 4, CTR_OUT = 5, CTR_MARK = 6, CTR_OWNED = 7, CTR_N = 8 };
 
 template <typename T>
 struct Dev {
@@ -67,6 +67,7 @@ struct Dev {
   // queued (null owner: one rank owns every site)
   const int* owner;      // [n] rank of each site, or null
   int rank;
+  int* own_order;        // [n] grid-order positions of the rank's own sites (CTR_OWNED of them), or null
   unsigned long long* outbox;
   long long ocap;
 };

@@ -529,6 +529,23 @@ __device__ __forceinline__ void knn_scan_shell(const GridView<T>& G, int lev, in
 // nearest is not certified by the scan gets its own nearest-site query.
 // knn2, r64 (optional): the 33rd..64th nearest (ids) and the certified radius of
 // the 64 (0 when the scan does not certify them).
+// grid-order positions of the rank's own sites (partitioned context), a warp's
+// positions in order, for the nearest-list pass
+template <typename T>
+__global__ void k_own_order(const __grid_constant__ Dev<T> C, int* order) {
+  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < C.n; t0 += (long long)gridDim.x * blockDim.x) {
+    long long t = t0 + threadIdx.x;
+    bool mine = t < C.n && owned(C, site_id(C.G.L[0].gs[t]));
+    unsigned m = __ballot_sync(FULL, mine);
+    if (!m) continue;
+    int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(C.ctr + CTR_OWNED, (unsigned long long)__popc(m));
+    base = __shfl_sync(FULL, base, 0);
+    if (mine) order[base + __popc(m & ((1u << lane) - 1u))] = (int)t;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ Dev<T> C, int* knn, float* knn_d2,
                                                         T* delta, int* knn2, float* r64) {
@@ -537,24 +554,16 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(const __grid_constant__ 
   KnnScratch& S = sh[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
   // each block takes a contiguous range of the sites in the grid's cell order, its
-  // warps interleaved, so that a block's warps scan neighbouring cells
-  long long per = ((long long)C.n + gridDim.x - 1) / gridDim.x;
-  long long t0 = (long long)blockIdx.x * per, t1 = t0 + per < C.n ? t0 + per : C.n;
+  // warps interleaved, so that a block's warps scan neighbouring cells.  A
+  // partitioned context without the split (own_order set) lists its own sites
+  // only: the others' pairs are clipped by other ranks, and nothing here reads
+  // their lists but the candidate ranking, which bounds every id it reads.
+  const long long N = C.own_order ? (long long)C.ctr[CTR_OWNED] : (long long)C.n;
+  long long per = (N + gridDim.x - 1) / gridDim.x;
+  long long t0 = (long long)blockIdx.x * per, t1 = t0 + per < N ? t0 + per : N;
   for (long long t = t0 + (threadIdx.x >> 5); t < t1; t += KNN_WARPS) {
-    const typename Prec<T>::V4 s4 = C.G.L[0].gs[t];
+    const typename Prec<T>::V4 s4 = C.G.L[0].gs[C.own_order ? (long long)C.own_order[t] : t];
     const int i = site_id(s4);
-    if (!C.split && !owned(C, i)) {
-      // partitioned without the split: only the rank's own pairs read lists; the
-      // others get empty, uncertified ones (the search then scans the grid)
-      knn[(long long)i * KNN + lane] = -1;
-      knn_d2[(long long)i * KNN + lane] = -1.f;
-      if (knn2) knn2[(long long)i * KNN + lane] = -1;
-      if (lane == 0) {
-        if (knn2) r64[i] = 0.f;
-        if (delta) delta[i] = T(1);
-      }
-      continue;
-    }
     T qx = s4.x, qy = s4.y, qz = s4.z;
     int cnt = 0;
     bool over = false;
