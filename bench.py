@@ -63,8 +63,8 @@ DESC = {
 # clip kernel, from a single-pass ncu capture of the learned form (top 24, split) on
 # the full workload,
 # valid only for the kernel sources it was taken on (their hash)
-FLOOD_TRAFFIC = {"source_hash": "538e2d8d59e2263a",
-                 "bytes": {"shell": 1.23e9 + 0.260e9}}
+FLOOD_TRAFFIC = {"source_hash": "5a5f82d27e94b648",
+                 "bytes": {"shell": 1.24e9 + 0.260e9}}
 
 
 def _source_hash():
