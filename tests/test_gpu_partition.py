@@ -19,6 +19,8 @@ KEYS = ("measure", "centroid", "nbr_off", "nbr_idx")
 CASES = [
     ("cube", 20000, dict(mapping=1)),
     ("cube", 20000, dict(learned=1, topk=16, mapping=1)),
+    ("cube", 20000, dict(mapping=2)),                                  # thread per pair
+    ("cube2m", 200000, dict(learned=1, topk=24, split=1, mapping=1)),
     ("shell", 30000, dict(learned=1, topk=24, mapping=1)),
     ("shell", 30000, dict(learned=1, topk=24, split=1, mapping=1)),
     ("box", 3000, dict(mapping=1)),
